@@ -1,0 +1,41 @@
+"""Sanity of the seeded workload generators (CPU only)."""
+import numpy as np
+
+from paper_2607_11952_gb300 import synth
+
+
+def test_ba_edge_count_and_determinism():
+    e = synth.barabasi_albert(1000, 3, synth.rng_for(1))
+    assert e.shape[0] == 3 * (1000 - 3)
+    e2 = synth.barabasi_albert(1000, 3, synth.rng_for(1))
+    np.testing.assert_array_equal(e, e2)
+    assert np.all(e[:, 0] < e[:, 1])
+
+
+def test_chung_lu_mean_degree():
+    for n, g, d in [(20000, 2.5, 8.0), (20000, 2.1, 10.0)]:
+        e = synth.chung_lu(n, g, d, synth.rng_for(3))
+        mean = 2 * e.shape[0] / n
+        assert abs(mean - d) / d < 0.05, mean
+        deg = np.bincount(e.ravel(), minlength=n)
+        assert deg.max() > 20 * d          # heavy tail
+
+
+def test_pair_truth_and_anchors():
+    g = synth.config_pair("ba1k")
+    assert g.n1 == g.n2 == 1000
+    assert g.anchors.shape[0] == 50
+    assert np.all(g.truth[g.anchors[:, 0]] == g.anchors[:, 1])
+    assert np.all(g.truth[g.test_pairs[:, 0]] == g.test_pairs[:, 1])
+    assert g.anchors.shape[0] + g.test_pairs.shape[0] == 1000
+    m1 = g.edges1.shape[0]
+    # 10% deleted and 5% added
+    assert g.edges2.shape[0] == m1 - round(0.10 * m1) + round(0.05 * m1)
+
+
+def test_induced_uneven_pair():
+    g = synth.config_pair("cl100k", n=2000)
+    assert g.n1 == 2000 and g.n2 == 1600
+    kept = np.nonzero(g.truth >= 0)[0]
+    assert kept.shape[0] == 1600
+    assert np.array_equal(np.sort(g.truth[kept]), np.arange(1600))
