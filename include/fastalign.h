@@ -1,0 +1,213 @@
+/*
+ * fastalign.h -- C ABI of the GB300 (sm_103a) implementation of the
+ * per-outer-iteration transport-plan update of FastAlign's OT-based network
+ * alignment ("Scalable Optimal Transport Algorithm for Network Alignment",
+ * Algorithm 1, Eq. 1-4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns fa_status and never aborts or throws.  On failure
+ *   fa_last_error_string() (per thread) describes the cause.
+ * - "host" pointers are read before the call returns.  "device" pointers
+ *   are CUDA device memory owned by the caller; the library never frees
+ *   them.  The library owns only what it allocates inside a handle
+ *   (fa_graph, fa_ctx, fa_gnn) and frees it in the matching *_destroy.
+ * - Calls that take a cudaStream_t enqueue their work on that stream and
+ *   return without synchronising, except where they return a host scalar
+ *   (fa_sinkhorn), which synchronises that stream only.
+ * - Dense n1 x n2 matrices are row-major with a padded leading dimension
+ *   ld = fa_ctx_ld(ctx) >= n2 (a multiple of 64 elements).  Padding columns
+ *   of the Gibbs kernel K are written as 0 and must stay 0.
+ * - The transport plan is held implicitly as
+ *       T_ij = exp(log_u_i) * K_ij * exp(log_v_j)
+ *   with K the row-stabilised Gibbs kernel (float32 or bfloat16 storage),
+ *   log_u (n1) and log_v (n2) float32 log-scalings.  These are the
+ *   exponentiated dual potentials of Eq. 3/Eq. 4 (b_i/eps and a_j/eps) up
+ *   to the stabilising row offsets folded into K.
+ */
+#ifndef FASTALIGN_H
+#define FASTALIGN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without pulling in the CUDA headers. */
+typedef struct CUstream_st* fa_stream_t;
+
+typedef enum {
+  FA_OK = 0,
+  FA_ERR_ARG = 1,            /* invalid argument (sizes, null pointers, bad graph) */
+  FA_ERR_OOM = 2,            /* a device allocation inside a handle failed */
+  FA_ERR_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+  FA_ERR_NOT_CONVERGED = 4,  /* fa_sinkhorn hit max_iter with err > tol */
+  FA_ERR_NUMERIC = 5,        /* NaN/Inf or an all-zero row/column was met */
+  FA_ERR_UNSUPPORTED = 6,    /* size or mode outside what the kernels support */
+  FA_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up */
+} fa_status;
+
+typedef enum { FA_F32 = 0, FA_BF16 = 1 } fa_dtype;
+
+/* GEMM engine for the node-similarity cost (Alg. 1 L4). */
+typedef enum {
+  FA_GEMM_AUTO = 0,      /* tcgen05: bf16 operands for FA_BF16, 3xTF32 split for FA_F32 */
+  FA_GEMM_TCGEN05 = 1,   /* same as AUTO */
+  FA_GEMM_SIMT = 2       /* plain FP32 CUDA-core GEMM (cross-check path) */
+} fa_gemm_mode;
+
+/* Hyper-parameters of Algorithm 1 (named in the paper, values unstated). */
+typedef struct {
+  int32_t dtype;              /* fa_dtype: storage type of the Gibbs kernel K */
+  float eps;                  /* entropic regulariser (Eq. 1, Eq. 3) */
+  float eps_anc;              /* eps inside C_anc = -log(eps_anc + OneHot(L)) (Alg. 1 L6) */
+  float alpha;                /* node-cost mix (Alg. 1 L4) */
+  float beta;                 /* RWR restart probability (Alg. 1 L3) */
+  int32_t k_rwr;              /* RWR iterations (Alg. 1 L3) */
+  int32_t k_prop;             /* C_node propagation steps A1bar C A2bar^T (Alg. 1 L5) */
+  float lam_e, lam_n, lam_a;  /* cost weights (Eq. 2) */
+  float lam_p;                /* proximal weight: C_eff = C - lam_p log T_prev */
+  float delta;                /* clamp inside -log(max(., delta)) of C_nbr */
+  int32_t normalize_features; /* 1: unit-L2 attribute rows before X1 X2^T */
+  int32_t gemm_mode;          /* fa_gemm_mode */
+} fa_params;
+
+/* Fills *p with the library defaults (eps = eps_anc = lam_p = 0.05,
+ * alpha = 0.5, beta = 0.15, k_rwr = 10, k_prop = 1, lam_e = 1,
+ * lam_n = lam_a = 0.05, delta = 1e-30, normalize_features = 1, FA_F32). */
+void fa_params_default(fa_params* p);
+
+typedef struct fa_graph fa_graph;
+typedef struct fa_ctx fa_ctx;
+
+/* ----------------------------------------------------------------------
+ * fa_build_graph -- Alg. 1 L1 (row normalisation, Section 3.3 sparse form).
+ * n: node count (>= 1).  src, dst: host int32 arrays of n_edges undirected
+ * edges; self-loops and duplicates are dropped, node ids must lie in
+ * [0, n) (FA_ERR_ARG otherwise).  Builds on the current device the CSR of
+ * the symmetric adjacency A (int32 row_ptr/col, columns sorted) with the
+ * values of Abar = D^-1 A and of Abar^T; degree-0 rows are empty.
+ * *out receives a handle freed by fa_graph_destroy.  Synchronous.
+ * -------------------------------------------------------------------- */
+fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
+                         const int32_t* dst, fa_graph** out);
+fa_status fa_graph_destroy(fa_graph* g);
+/* n and nnz (= 2 x unique undirected edges) of a built graph. */
+fa_status fa_graph_info(const fa_graph* g, int32_t* n, int64_t* nnz);
+
+/* ----------------------------------------------------------------------
+ * fa_ctx_create -- an alignment context for the pair (g1, g2).  Copies
+ * *params, allocates the device workspaces of the outer iteration (the
+ * transposed left-product buffer, the log-kernel scratch, partial sums).
+ * The graphs must outlive the context.  fa_ctx_ld gives the padded leading
+ * dimension ld of every n1 x n2 matrix passed to the other calls;
+ * fa_ctx_workspace_bytes the device bytes the context holds.
+ * -------------------------------------------------------------------- */
+fa_status fa_ctx_create(const fa_graph* g1, const fa_graph* g2,
+                        const fa_params* params, fa_ctx** out);
+fa_status fa_ctx_destroy(fa_ctx* ctx);
+int64_t fa_ctx_ld(const fa_ctx* ctx);
+int64_t fa_ctx_workspace_bytes(const fa_ctx* ctx);
+
+/* ----------------------------------------------------------------------
+ * fa_node_cost -- Phase 1 of Algorithm 1 (L2-L7):
+ *   R_g  <- k_rwr steps of (1-beta) Abar_g R_g + beta R_g^(0)     (L2-L3)
+ *   C_node = alpha exp(-R1 R2^T) + (1-alpha) exp(-X1h X2h^T)      (L4)
+ *   C_node <- k_prop steps of A1bar C_node A2bar^T                 (L5)
+ *   C1 = (R1 R1^T) .* A1bar,  C2 = (R2 R2^T) .* A2bar^T  (SDDMM)    (L7)
+ * X1 (n1 x d), X2 (n2 x d): device float32 row-major attributes (d >= 1,
+ * may be NULL with d = 0 to drop the attribute term's variation: exp(0)).
+ * anchors: host int32 [n_anchor][2] pairs (i, j); 0 <= n_anchor.
+ * C_node: device float32 n1 x ld output (padding columns set to 0).
+ * C1/C2 values and the anchor list stay in ctx for fa_align_iter.
+ * The GEMM runs on tcgen05 tensor cores (see fa_gemm_mode).
+ * -------------------------------------------------------------------- */
+fa_status fa_node_cost(fa_ctx* ctx, const float* X1, const float* X2,
+                       int32_t d, const int32_t* anchors, int32_t n_anchor,
+                       float* C_node, fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * fa_plan_init -- the independent coupling T0 = mu nu^T (mu = 1/n1,
+ * nu = 1/n2, Section 2.1): K = 1 (0 in padding), log_u = log mu,
+ * log_v = log nu.  K: device n1 x ld of params.dtype; log_u (n1), log_v
+ * (n2): device float32.
+ * -------------------------------------------------------------------- */
+fa_status fa_plan_init(fa_ctx* ctx, void* K, float* log_u, float* log_v,
+                       fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * fa_align_iter -- Phase 2 of one outer iteration (Alg. 1 L10-L12) and
+ * the Gibbs kernel of the proximal step:
+ *   W   = P1 T_prev           P1 in {C1, A1bar^T}        (left SpMMs)
+ *   Z   = W P2^T              P2 in {C2, A2bar^T}         (right SpMMs)
+ *   C   = C_node + lam_e Z_e - lam_n log max(Z_n, delta) + lam_a C_anc
+ *   log K_new = -C/eps + (lam_p/eps) log T_prev,  row-max stabilised
+ * then the first Sinkhorn column update a_1 (Eq. 3, Alg. 1 L14) from the
+ * row-stabilised start b0.
+ * In:  K (T_prev's kernel), log_u, log_v, C_node (from fa_node_cost).
+ * Out: K overwritten in place by the new row-stabilised kernel (row max 1),
+ *      log_u = 0, log_v = a_1 / eps.
+ * -------------------------------------------------------------------- */
+fa_status fa_align_iter(fa_ctx* ctx, void* K, float* log_u, float* log_v,
+                        const float* C_node, fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * fa_sinkhorn -- Phase 3 (Alg. 1 L13-L16, Eq. 3) on a fixed kernel K.
+ * One fused sweep per iteration reads K once: the row update
+ * u_i = mu_i / sum_j K_ij v_j (b update) and, in the same pass, the column
+ * sums sum_i K_ij u_i for the next column update (a update).  The L1
+ * marginal error |T^T 1 - nu|_1 of the plan after each b update is
+ * computed in FP64 on the device.
+ * In: log_v holds the current column scaling (a_1 from fa_align_iter) unless
+ *     warm_log_v (device n2 float32, nullable) is given, which replaces it.
+ * Runs until err <= tol at a checked iteration (every check_every
+ * iterations; tol < 0 disables the check) or max_iter iterations.
+ * Out: log_u, log_v of the last completed iteration (a_t, b_t); *iters_out,
+ *      *err_out (host, nullable) its count and error.
+ * Returns FA_ERR_NOT_CONVERGED (state still valid) when tol >= 0 and the
+ * cap was hit, FA_ERR_NUMERIC on NaN/Inf or an all-zero row or column.
+ * Synchronises the stream when it reads the error back.
+ * -------------------------------------------------------------------- */
+fa_status fa_sinkhorn(fa_ctx* ctx, const void* K, float* log_u, float* log_v,
+                      const float* warm_log_v, int32_t max_iter, double tol,
+                      int32_t check_every, int32_t* iters_out, double* err_out,
+                      fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * fa_topk -- alignment read-out (Eq. 4, Section 4.1.1): per row i the k
+ * columns with the largest T_ij (ties to the lower j).  1 <= k <= 32.
+ * idx: device int32 n1 x k; score: device float32 n1 x k (T_ij / u_i,
+ * i.e. K_ij v_j), nullable.
+ * -------------------------------------------------------------------- */
+fa_status fa_topk(fa_ctx* ctx, const void* K, const float* log_v, int32_t k,
+                  int32_t* idx, float* score, fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * fa_rank -- 1-based rank of column cols[t] in row rows[t] under the same
+ * order as fa_topk: 1 + #{j: T_ij > T_ic} + #{j < c: T_ij == T_ic}
+ * (Section 4.1.1, Hits@K and MRR).  rows, cols, rank_out: device int32
+ * arrays of n_query entries.
+ * -------------------------------------------------------------------- */
+fa_status fa_rank(fa_ctx* ctx, const void* K, const float* log_v,
+                  int32_t n_query, const int32_t* rows, const int32_t* cols,
+                  int32_t* rank_out, fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * Kernel-level timing of the last fa_sinkhorn call: average device time of
+ * one fused sweep (ms), measured with CUDA events on the call's stream
+ * when enabled by fa_ctx_set_timing(ctx, 1).
+ * -------------------------------------------------------------------- */
+fa_status fa_ctx_set_timing(fa_ctx* ctx, int32_t on);
+fa_status fa_ctx_last_sweep_ms(const fa_ctx* ctx, double* ms, int32_t* n);
+
+/* Per-thread description of the last error. */
+const char* fa_last_error_string(void);
+
+/* Number of kernels this library launched since load (all entry points). */
+int64_t fa_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTALIGN_H */

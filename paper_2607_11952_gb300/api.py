@@ -1,0 +1,176 @@
+"""Python front end of the GB300 FastAlign hot path.
+
+``Graph`` and ``Aligner`` own the device buffers (torch tensors, used for
+memory and streams only) and call the C ABI through ``_lib``; every step of
+the method runs in the CUDA kernels of libfastalign.so.
+
+Typical use (Algorithm 1):
+
+    g1, g2 = Graph(n1, edges1), Graph(n2, edges2)
+    al = Aligner(g1, g2, Params(dtype="bf16"))
+    al.node_cost(X1, X2, anchors)          # Phase 1 (L1-L7)
+    al.plan_init()                         # S0 = mu nu^T
+    for t in range(T):                     # outer iterations
+        al.align_iter()                    # Phase 2 (L10-L12) + Gibbs kernel
+        al.sinkhorn(max_iter=50)           # Phase 3 (L13-L16, Eq. 3)
+    idx, score = al.topk(10)               # read-out (Section 4.1.1)
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+@dataclasses.dataclass
+class Params:
+    """Mirror of ``fa_params`` (defaults from ``fa_params_default``)."""
+    dtype: str = "f32"              # storage of the Gibbs kernel: "f32" | "bf16"
+    eps: float = 0.05
+    eps_anc: float = 0.05
+    alpha: float = 0.5
+    beta: float = 0.15
+    k_rwr: int = 10
+    k_prop: int = 1
+    lam_e: float = 1.0
+    lam_n: float = 0.05
+    lam_a: float = 0.05
+    lam_p: float = 0.05
+    delta: float = 1e-30
+    normalize_features: bool = True
+    gemm: str = "auto"              # "auto" | "tcgen05" | "simt"
+
+    def to_c(self) -> L.fa_params:
+        p = L.fa_params_default()
+        p.dtype = {"f32": L.FA_F32, "bf16": L.FA_BF16}[self.dtype]
+        for f in ("eps", "eps_anc", "alpha", "beta", "lam_e", "lam_n", "lam_a",
+                  "lam_p", "delta"):
+            setattr(p, f, float(getattr(self, f)))
+        p.k_rwr = int(self.k_rwr)
+        p.k_prop = int(self.k_prop)
+        p.normalize_features = 1 if self.normalize_features else 0
+        p.gemm_mode = {"auto": L.FA_GEMM_AUTO, "tcgen05": L.FA_GEMM_TCGEN05,
+                       "simt": L.FA_GEMM_SIMT}[self.gemm]
+        return p
+
+
+class Graph:
+    """Device CSR of an undirected graph (fa_build_graph)."""
+
+    def __init__(self, n: int, edges: np.ndarray):
+        e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+        self.n = int(n)
+        self.handle = L.fa_build_graph(self.n, e[:, 0].astype(np.int32),
+                                       e[:, 1].astype(np.int32))
+        self.nnz = L.fa_graph_info(self.handle)[1]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.fa_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Aligner:
+    """Holds one alignment context and the plan T = diag(e^log_u) K diag(e^log_v)."""
+
+    def __init__(self, g1: Graph, g2: Graph, params: Params | None = None,
+                 device: str | torch.device = "cuda"):
+        self.g1, self.g2 = g1, g2
+        self.params = params or Params()
+        self.device = torch.device(device)
+        self.ctx = L.fa_ctx_create(g1.handle, g2.handle, self.params.to_c())
+        self.n1, self.n2 = g1.n, g2.n
+        self.ld = L.fa_ctx_ld(self.ctx)
+        kdt = torch.bfloat16 if self.params.dtype == "bf16" else torch.float32
+        self.K = torch.empty((self.n1, self.ld), dtype=kdt, device=self.device)
+        self.C_node = torch.empty((self.n1, self.ld), dtype=torch.float32, device=self.device)
+        self.log_u = torch.empty(self.n1, dtype=torch.float32, device=self.device)
+        self.log_v = torch.empty(self.n2, dtype=torch.float32, device=self.device)
+
+    # -- Phase 1
+    def node_cost(self, X1, X2, anchors: np.ndarray, stream=None):
+        X1 = torch.as_tensor(X1, dtype=torch.float32).to(self.device).contiguous()
+        X2 = torch.as_tensor(X2, dtype=torch.float32).to(self.device).contiguous()
+        d = X1.shape[1] if X1.ndim == 2 else 0
+        L.fa_node_cost(self.ctx, X1 if d else None, X2 if d else None, d,
+                       np.asarray(anchors), self.C_node, stream)
+
+    def plan_init(self, stream=None):
+        L.fa_plan_init(self.ctx, self.K, self.log_u, self.log_v, stream)
+
+    # -- Phase 2
+    def align_iter(self, stream=None):
+        L.fa_align_iter(self.ctx, self.K, self.log_u, self.log_v, self.C_node, stream)
+
+    # -- Phase 3
+    def sinkhorn(self, max_iter: int, tol: float = -1.0, check_every: int = 1,
+                 warm_log_v=None, stream=None):
+        """Returns (iterations, marginal error, status)."""
+        return L.fa_sinkhorn(self.ctx, self.K, self.log_u, self.log_v, warm_log_v,
+                             max_iter, tol, check_every, stream)
+
+    # -- read-out
+    def topk(self, k: int, stream=None):
+        idx = torch.empty((self.n1, k), dtype=torch.int32, device=self.device)
+        score = torch.empty((self.n1, k), dtype=torch.float32, device=self.device)
+        L.fa_topk(self.ctx, self.K, self.log_v, k, idx, score, stream)
+        return idx, score
+
+    def rank(self, rows, cols, stream=None):
+        r = torch.as_tensor(np.asarray(rows), dtype=torch.int32).to(self.device)
+        c = torch.as_tensor(np.asarray(cols), dtype=torch.int32).to(self.device)
+        out = torch.empty_like(r)
+        L.fa_rank(self.ctx, self.K, self.log_v, r, c, out, stream)
+        return out
+
+    def hits_mrr(self, test_pairs: np.ndarray, ks=(1, 10)):
+        r = self.rank(test_pairs[:, 0], test_pairs[:, 1]).cpu().numpy()
+        out = {f"hits@{k}": float(np.mean(r <= k)) for k in ks}
+        out["mrr"] = float(np.mean(1.0 / r))
+        return out
+
+    def plan_f64(self) -> np.ndarray:
+        """The plan as a host float64 array (for checks; n1 x n2)."""
+        K = self.K[:, : self.n2].float().cpu().double().numpy()
+        u = np.exp(self.log_u.cpu().double().numpy())
+        v = np.exp(self.log_v.cpu().double().numpy())
+        return u[:, None] * K * v[None, :]
+
+    def set_timing(self, on: bool = True):
+        L.fa_ctx_set_timing(self.ctx, on)
+
+    def last_sweep_ms(self):
+        return L.fa_ctx_last_sweep_ms(self.ctx)
+
+    def align(self, X1, X2, anchors, n_outer: int, n_sink: int, tol: float = -1.0,
+              check_every: int = 1, warm=None):
+        """Algorithm 1 end to end; returns per-outer (iterations, error)."""
+        self.node_cost(X1, X2, anchors)
+        self.plan_init()
+        hist = []
+        for _ in range(n_outer):
+            self.align_iter()
+            w = warm(self) if warm is not None else None
+            it, err, st = self.sinkhorn(n_sink, tol, check_every, w)
+            hist.append((it, err, st))
+        return hist
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            L.fa_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,476 @@
+// Sparse x dense kernels of FastAlign (Section 3.3, "sparsity-aware"):
+//   - RWR positional encoding, Alg. 1 L3 (SpMM with a tall-skinny dense R)
+//   - SDDMM for the intra-network costs C1, C2, Alg. 1 L7
+//   - the "SpMM on a wide dense matrix" pair  Z = P1 . D . P2^T
+//     (Section 3.4; Alg. 1 L5, L10, L11), split into
+//       left:  W  = P1 D   (row gathers of D, stored transposed as W^T)
+//       right: Z  = W P2^T (row gathers of W^T), with a fused epilogue that
+//              either stores Z (C_node propagation, Alg. 1 L5) or assembles
+//              the cost (Alg. 1 L12, Eq. 2) and the log Gibbs kernel of the
+//              proximal step.
+// Storing the left product transposed turns both halves of the triple
+// product into coalesced row gathers; the CTA order keeps one column panel
+// of the gathered operand resident in L2 while every row tile uses it (the
+// GPU form of the paper's column-blocked SpMM, Section 3.4).
+#include <math.h>
+
+#include "fa_internal.cuh"
+
+namespace fa {
+
+// ------------------------------------------------------------ small helpers
+__global__ void k_fill(float* p, int64_t n, float v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) p[i] = v;
+}
+
+fa_status launch_fill(float* p, int64_t n, float v, cudaStream_t s) {
+  if (n <= 0) return FA_OK;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_fill<<<(unsigned)blocks, 256, 0, s>>>(p, n, v);
+  FA_LAUNCHED("k_fill");
+  return FA_OK;
+}
+
+__global__ void k_exp_vec(int n, const float* __restrict__ x, float* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = expf(x[i]);
+}
+
+fa_status launch_exp_vec(int n, const float* x, float* y, cudaStream_t s) {
+  if (n <= 0) return FA_OK;
+  k_exp_vec<<<(n + 255) / 256, 256, 0, s>>>(n, x, y);
+  FA_LAUNCHED("k_exp_vec");
+  return FA_OK;
+}
+
+// ------------------------------------------------------------ RWR (Alg. 1 L3)
+// Rout[i,:] = (1-beta) sum_k Abar[i,k] Rin[k,:]; the beta R^(0) term is
+// added afterwards by k_add_onehot.  One warp per row, float4 over columns.
+__global__ void __launch_bounds__(256) k_rwr_step(
+    int n, int L, int64_t ldr, const int32_t* __restrict__ rp,
+    const int32_t* __restrict__ ci, const float* __restrict__ val, float c,
+    const float* __restrict__ Rin, float* __restrict__ Rout) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int e0 = rp[warp], e1 = rp[warp + 1];
+  const int nv = (int)(ldr / 4);
+  float4* out = reinterpret_cast<float4*>(Rout + (int64_t)warp * ldr);
+  for (int c0 = lane; c0 < nv; c0 += 32) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = e0; e < e1; ++e) {
+      const float w = val[e];
+      const float4 r = __ldg(reinterpret_cast<const float4*>(Rin + (int64_t)ci[e] * ldr) + c0);
+      acc.x += w * r.x; acc.y += w * r.y; acc.z += w * r.z; acc.w += w * r.w;
+    }
+    acc.x *= c; acc.y *= c; acc.z *= c; acc.w *= c;
+    out[c0] = acc;
+  }
+}
+
+fa_status launch_rwr_step(const DevGraph& g, int L, int64_t ldr, float beta,
+                          const float* Rin, float* Rout, cudaStream_t s) {
+  int64_t threads = (int64_t)g.n * 32;
+  k_rwr_step<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      g.n, L, ldr, g.row_ptr, g.col, g.val_row, 1.0f - beta, Rin, Rout);
+  FA_LAUNCHED("k_rwr_step");
+  return FA_OK;
+}
+
+// R[nodes[l], l] += value  (the beta R^(0) term; R^(0) is one-hot, Alg. 1 L2)
+__global__ void k_add_onehot(int L, int64_t ldr, const int32_t* __restrict__ nodes,
+                             float value, float* __restrict__ R) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < L) R[(int64_t)nodes[l] * ldr + l] += value;
+}
+
+fa_status launch_add_onehot(int L, int64_t ldr, const int32_t* nodes,
+                            float value, float* R, cudaStream_t s) {
+  if (L <= 0) return FA_OK;
+  k_add_onehot<<<(L + 255) / 256, 256, 0, s>>>(L, ldr, nodes, value, R);
+  FA_LAUNCHED("k_add_onehot");
+  return FA_OK;
+}
+
+fa_status launch_onehot(int n, int L, int64_t ldr, const int32_t* nodes,
+                        float* R, cudaStream_t s) {
+  FA_TRY(launch_fill(R, (int64_t)n * ldr, 0.0f, s));
+  return launch_add_onehot(L, ldr, nodes, 1.0f, R, s);
+}
+
+// ------------------------------------------------------------ SDDMM (Alg. 1 L7)
+// out[e] = w[e] * <R[i,:], R[k,:]> for every stored entry e = (i, k); w is
+// Abar (1/deg i) for C1 = (R1 R1^T) .* Abar1 or Abar^T (1/deg k) for
+// C2 = (R2 R2^T) .* Abar2^T.  One warp per row, lanes over the L columns.
+__global__ void __launch_bounds__(256) k_sddmm(
+    int n, int64_t ldr, const int32_t* __restrict__ rp,
+    const int32_t* __restrict__ ci, const float* __restrict__ w,
+    const float* __restrict__ R, float* __restrict__ out) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int nv = (int)(ldr / 4);
+  const float4* ri = reinterpret_cast<const float4*>(R + (int64_t)warp * ldr);
+  for (int e = rp[warp]; e < rp[warp + 1]; ++e) {
+    const float4* rk = reinterpret_cast<const float4*>(R + (int64_t)ci[e] * ldr);
+    float acc = 0.f;
+    for (int c0 = lane; c0 < nv; c0 += 32) {
+      float4 a = __ldg(ri + c0), b = __ldg(rk + c0);
+      acc += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[e] = w[e] * acc;
+  }
+}
+
+fa_status launch_sddmm(const DevGraph& g, int L, int64_t ldr, const float* R,
+                       bool weight_by_col, float* out, cudaStream_t s) {
+  if (g.nnz == 0) return FA_OK;
+  int64_t threads = (int64_t)g.n * 32;
+  k_sddmm<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      g.n, ldr, g.row_ptr, g.col, weight_by_col ? g.val_col : g.val_row, R, out);
+  FA_LAUNCHED("k_sddmm");
+  return FA_OK;
+}
+
+// ------------------------------------------------------------ attributes
+// Xh[i,:] = X[i,:] / |X[i,:]|_2 (or a plain copy), zero rows stay zero,
+// padding columns [d, ldx) set to 0.  One warp per row.
+__global__ void k_normalize_rows(int n, int d, const float* __restrict__ X,
+                                 int64_t ldx, int normalize,
+                                 float* __restrict__ Xh) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const float* x = X + (int64_t)warp * d;
+  float ss = 0.f;
+  for (int c = lane; c < d; c += 32) ss += x[c] * x[c];
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  float scale = 1.0f;
+  if (normalize) scale = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+  for (int c = lane; c < ldx; c += 32)
+    Xh[(int64_t)warp * ldx + c] = c < d ? x[c] * scale : 0.f;
+}
+
+fa_status launch_normalize_rows(int n, int d, const float* X, int64_t ldx,
+                                bool normalize, float* Xh, cudaStream_t s) {
+  int64_t threads = (int64_t)n * 32;
+  k_normalize_rows<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      n, d, X, ldx, normalize ? 1 : 0, Xh);
+  FA_LAUNCHED("k_normalize_rows");
+  return FA_OK;
+}
+
+// ------------------------------------------------------------ left SpMM
+// W^T[j, i] = sum_k P[i,k] s_k D[k, j]  for NV value sets P in {va, vb}.
+// CTA tile: 32 rows i x 64 columns j.  Warp w computes rows 4w..4w+3, lane l
+// columns 2l, 2l+1 (one 128/256-byte coalesced gather per neighbour row),
+// then the tile is transposed through shared memory and stored as 32
+// consecutive i per column j (NV floats per element).  blockIdx.x runs over
+// row tiles first, so all row tiles of one 64-column panel of D run
+// back-to-back and the panel (n1 x 64 elements) stays in L2.
+template <int NV> struct VecF;
+template <> struct VecF<1> { using T = float; };
+template <> struct VecF<2> { using T = float2; };
+
+__device__ __forceinline__ float2 load_pair(const float* p) {
+  return __ldg(reinterpret_cast<const float2*>(p));
+}
+__device__ __forceinline__ float2 load_pair(const __nv_bfloat16* p) {
+  __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
+  return __bfloat1622float2(v);
+}
+
+template <typename TD, int NV>
+__global__ void __launch_bounds__(256) k_spmm_left_T(
+    int n1, int n2, int64_t ldd, int64_t ldw, const int32_t* __restrict__ rp,
+    const int32_t* __restrict__ ci, const float* __restrict__ va,
+    const float* __restrict__ vb, const float* __restrict__ scale,
+    const TD* __restrict__ D, float* __restrict__ Wt) {
+  constexpr int TI = 32, TJ = 64, PAD = (NV == 1) ? 1 : 2;
+  __shared__ float tile[TI][TJ * NV + PAD];
+  const int i0 = blockIdx.x * TI;
+  const int j0 = blockIdx.y * TJ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TD* dcol = D + j0 + 2 * lane;
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) {
+    const int r = warp * 4 + rr;
+    const int i = i0 + r;
+    float a0[NV], a1[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a0[v] = a1[v] = 0.f;
+    if (i < n1) {
+      const int e0 = rp[i], e1 = rp[i + 1];
+      int e = e0;
+      for (; e + 2 <= e1; e += 2) {
+        const int k0 = ci[e], k1 = ci[e + 1];
+        float s0 = scale ? scale[k0] : 1.f, s1 = scale ? scale[k1] : 1.f;
+        const float2 d0 = load_pair(dcol + (int64_t)k0 * ldd);
+        const float2 d1 = load_pair(dcol + (int64_t)k1 * ldd);
+        float w0 = va[e] * s0, w1 = va[e + 1] * s1;
+        a0[0] += w0 * d0.x + w1 * d1.x;
+        a1[0] += w0 * d0.y + w1 * d1.y;
+        if (NV == 2) {
+          float x0 = vb[e] * s0, x1 = vb[e + 1] * s1;
+          a0[NV - 1] += x0 * d0.x + x1 * d1.x;
+          a1[NV - 1] += x0 * d0.y + x1 * d1.y;
+        }
+      }
+      for (; e < e1; ++e) {
+        const int k0 = ci[e];
+        float s0 = scale ? scale[k0] : 1.f;
+        const float2 d0 = load_pair(dcol + (int64_t)k0 * ldd);
+        float w0 = va[e] * s0;
+        a0[0] += w0 * d0.x;
+        a1[0] += w0 * d0.y;
+        if (NV == 2) {
+          float x0 = vb[e] * s0;
+          a0[NV - 1] += x0 * d0.x;
+          a1[NV - 1] += x0 * d0.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      tile[r][(2 * lane) * NV + v] = a0[v];
+      tile[r][(2 * lane + 1) * NV + v] = a1[v];
+    }
+  }
+  __syncthreads();
+  // transposed store: warp w writes columns c = w, w+8, ...; lane = row
+  using VT = typename VecF<NV>::T;
+  for (int c = warp; c < TJ; c += 8) {
+    const int j = j0 + c;
+    if (j >= n2) break;
+    VT* dst = reinterpret_cast<VT*>(Wt + ((int64_t)j * ldw + i0) * NV);
+    if constexpr (NV == 1) {
+      dst[lane] = tile[lane][c];
+    } else {
+      dst[lane] = make_float2(tile[lane][c * 2], tile[lane][c * 2 + 1]);
+    }
+  }
+}
+
+fa_status launch_spmm_left_T(const DevGraph& g1, int n2, int64_t ldd,
+                             int64_t ldw, const float* va, const float* vb,
+                             const float* scale, const void* D, bool d_bf16,
+                             float* Wt, cudaStream_t s) {
+  dim3 grid((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 63) / 64));
+  const bool two = vb != nullptr;
+  if (d_bf16) {
+    auto* Dp = static_cast<const __nv_bfloat16*>(D);
+    if (two) k_spmm_left_T<__nv_bfloat16, 2><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+    else     k_spmm_left_T<__nv_bfloat16, 1><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+  } else {
+    auto* Dp = static_cast<const float*>(D);
+    if (two) k_spmm_left_T<float, 2><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+    else     k_spmm_left_T<float, 1><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+  }
+  FA_LAUNCHED("k_spmm_left_T");
+  return FA_OK;
+}
+
+// ------------------------------------------------------------ right SpMM
+// Z[i, j] = sum_{l in N2(j)} Q[j,l] s_l W^T[l, i].  CTA tile: 64 columns j x
+// 32 rows i; warp w owns columns j0+8w..j0+8w+7, lane = row offset, so each
+// neighbour l is one coalesced 128/256-byte gather of W^T[l, i0:i0+32] and
+// every lane ends up holding 8 consecutive outputs of its own row -- the
+// epilogue needs no transpose.  blockIdx.x runs over column tiles first so
+// the W^T panel of one row tile (n2 x 32 elements) stays in L2.
+template <int NV>
+__device__ __forceinline__ void right_accumulate(
+    int j, int n2, int64_t ldw, int i0, int lane,
+    const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+    const float* __restrict__ qa, const float* __restrict__ qb,
+    const float* __restrict__ scale, const float* __restrict__ Wt,
+    float& za, float& zb) {
+  za = 0.f;
+  zb = 0.f;
+  if (j >= n2) return;
+  const int e0 = rp[j], e1 = rp[j + 1];
+  const float* base = Wt + (int64_t)(i0 + lane) * NV;
+  int e = e0;
+  for (; e + 2 <= e1; e += 2) {
+    const int l0 = ci[e], l1 = ci[e + 1];
+    const float s0 = scale ? scale[l0] : 1.f, s1 = scale ? scale[l1] : 1.f;
+    if constexpr (NV == 1) {
+      float w0 = __ldg(base + (int64_t)l0 * ldw);
+      float w1 = __ldg(base + (int64_t)l1 * ldw);
+      za += qa[e] * s0 * w0 + qa[e + 1] * s1 * w1;
+    } else {
+      float2 w0 = __ldg(reinterpret_cast<const float2*>(base + (int64_t)l0 * ldw * 2));
+      float2 w1 = __ldg(reinterpret_cast<const float2*>(base + (int64_t)l1 * ldw * 2));
+      za += qa[e] * s0 * w0.x + qa[e + 1] * s1 * w1.x;
+      zb += qb[e] * s0 * w0.y + qb[e + 1] * s1 * w1.y;
+    }
+  }
+  for (; e < e1; ++e) {
+    const int l0 = ci[e];
+    const float s0 = scale ? scale[l0] : 1.f;
+    if constexpr (NV == 1) {
+      za += qa[e] * s0 * __ldg(base + (int64_t)l0 * ldw);
+    } else {
+      float2 w0 = __ldg(reinterpret_cast<const float2*>(base + (int64_t)l0 * ldw * 2));
+      za += qa[e] * s0 * w0.x;
+      zb += qb[e] * s0 * w0.y;
+    }
+  }
+}
+
+// C_node propagation (Alg. 1 L5): plain store of Z.
+__global__ void __launch_bounds__(256) k_spmm_right_prop(
+    int n1, int n2, int64_t ldw, const int32_t* __restrict__ rp,
+    const int32_t* __restrict__ ci, const float* __restrict__ qa,
+    const float* __restrict__ Wt, float* __restrict__ C, int64_t ldc) {
+  const int j0 = blockIdx.x * 64, i0 = blockIdx.y * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int jb = j0 + warp * 8;
+  float z[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float zb;
+    right_accumulate<1>(jb + q, n2, ldw, i0, lane, rp, ci, qa, nullptr,
+                        nullptr, Wt, z[q], zb);
+  }
+  const int i = i0 + lane;
+  if (i < n1) {
+    float4* dst = reinterpret_cast<float4*>(C + (int64_t)i * ldc + jb);
+    dst[0] = make_float4(z[0], z[1], z[2], z[3]);
+    dst[1] = make_float4(z[4], z[5], z[6], z[7]);
+  }
+}
+
+fa_status launch_spmm_right_prop(const DevGraph& g2, int n1, int64_t ldw,
+                                 const float* qa, const float* Wt, float* C,
+                                 int64_t ldc, cudaStream_t s) {
+  dim3 grid((unsigned)(ldc / 64), (unsigned)((n1 + 31) / 32));
+  k_spmm_right_prop<<<grid, 256, 0, s>>>(n1, g2.n, ldw, g2.row_ptr, g2.col,
+                                         qa, Wt, C, ldc);
+  FA_LAUNCHED("k_spmm_right_prop");
+  return FA_OK;
+}
+
+// Cost assembly + log Gibbs kernel (Alg. 1 L10-L12, Eq. 2, proximal step):
+//   C   = C_node + lam_e Z_e - lam_n log max(Z_n, delta) + lam_a C_anc
+//   x   = -C/eps + (lam_p/eps) (log u_i + log K_prev_ij + log v_j)
+// stored as float32, plus the per-(row, 64-column tile) maximum of x.
+__device__ __forceinline__ void load8(const float* p, float (&k)[8]) {
+  float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+  k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+}
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, float (&k)[8]) {
+  uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float2 f = __bfloat1622float2(h[q]);
+    k[2 * q] = f.x;
+    k[2 * q + 1] = f.y;
+  }
+}
+
+template <typename TK>
+__global__ void __launch_bounds__(256) k_spmm_right_cost(
+    int n1, int n2, int64_t ldw, int64_t ldo, const int32_t* __restrict__ rp,
+    const int32_t* __restrict__ ci, const float* __restrict__ qa,
+    const float* __restrict__ qb, const float* __restrict__ scale,
+    const float* __restrict__ Wt, CostEpi ep) {
+  __shared__ float smax[8][32];
+  const int j0 = blockIdx.x * 64, i0 = blockIdx.y * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int jb = j0 + warp * 8;
+  float ze[8], zn[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    right_accumulate<2>(jb + q, n2, ldw, i0, lane, rp, ci, qa, qb, scale, Wt,
+                        ze[q], zn[q]);
+  const int i = i0 + lane;
+  float mx = -INFINITY;
+  if (i < n1) {
+    float cn[8], kp[8];
+    load8(ep.C_node + (int64_t)i * ldo + jb, cn);
+    load8(static_cast<const TK*>(ep.K_prev) + (int64_t)i * ldo + jb, kp);
+    const float lu = ep.log_u[i];
+    const float inv_eps = 1.0f / ep.eps;
+    const float prox = ep.lam_p * inv_eps;
+    const float c_off = -logf(ep.eps_anc);          // C_anc off the anchors
+    const float c_on = -logf(ep.eps_anc + 1.0f);    // C_anc on an anchor
+    const int a0 = ep.anc_ptr[i], a1 = ep.anc_ptr[i + 1];
+    float x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = jb + q;
+      if (j < n2) {
+        float canc = c_off;
+        for (int a = a0; a < a1; ++a)
+          if (ep.anc_col[a] == j) canc = c_on;
+        const float C = cn[q] + ep.lam_e * ze[q] -
+                        ep.lam_n * logf(fmaxf(zn[q], ep.delta)) +
+                        ep.lam_a * canc;
+        float xv = -C * inv_eps;
+        if (prox != 0.f) xv += prox * (lu + logf(kp[q]) + ep.log_v[j]);
+        x[q] = xv;
+        mx = fmaxf(mx, xv);
+      } else {
+        x[q] = -INFINITY;
+      }
+    }
+    float4* dst = reinterpret_cast<float4*>(ep.X + (int64_t)i * ldo + jb);
+    dst[0] = make_float4(x[0], x[1], x[2], x[3]);
+    dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+  }
+  smax[warp][lane] = mx;
+  __syncthreads();
+  if (warp == 0) {
+    float m = smax[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, smax[w][lane]);
+    if (i < n1) ep.rowmax_part[(int64_t)blockIdx.x * n1 + i] = m;
+  }
+}
+
+fa_status launch_spmm_right_cost(const DevGraph& g2, int n1, int64_t ldw,
+                                 int64_t ldo, const float* qa, const float* qb,
+                                 const float* scale, const float* Wt,
+                                 const CostEpi& ep, bool k_bf16,
+                                 cudaStream_t s) {
+  dim3 grid((unsigned)(ldo / 64), (unsigned)((n1 + 31) / 32));
+  if (k_bf16)
+    k_spmm_right_cost<__nv_bfloat16><<<grid, 256, 0, s>>>(
+        n1, g2.n, ldw, ldo, g2.row_ptr, g2.col, qa, qb, scale, Wt, ep);
+  else
+    k_spmm_right_cost<float><<<grid, 256, 0, s>>>(
+        n1, g2.n, ldw, ldo, g2.row_ptr, g2.col, qa, qb, scale, Wt, ep);
+  FA_LAUNCHED("k_spmm_right_cost");
+  return FA_OK;
+}
+
+// rowmax[i] = max over column tiles of the partial maxima.  An all -inf row
+// (every entry underflowed) is reported and pinned to 0.
+__global__ void k_rowmax_reduce(int n1, int ntiles, const float* __restrict__ part,
+                                float* __restrict__ rowmax, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n1) return;
+  float m = -INFINITY;
+  for (int t = 0; t < ntiles; ++t) m = fmaxf(m, part[(int64_t)t * n1 + i]);
+  if (!(m > -INFINITY) || isnan(m)) {
+    atomicOr(status, ST_NUMERIC);
+    m = 0.f;
+  }
+  rowmax[i] = m;
+}
+
+fa_status launch_rowmax_reduce(int n1, int ntiles, const float* part,
+                               float* rowmax, int* status, cudaStream_t s) {
+  k_rowmax_reduce<<<(n1 + 255) / 256, 256, 0, s>>>(n1, ntiles, part, rowmax, status);
+  FA_LAUNCHED("k_rowmax_reduce");
+  return FA_OK;
+}
+
+}  // namespace fa
