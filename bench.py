@@ -1,0 +1,358 @@
+"""Benchmark of the GB300 FastAlign hot path (one JSON line on stdout).
+
+Workload: the 50k-node Chung-Lu pair (exponent 2.1, mean degree 10, 15% edge
+noise, 128-dim attributes, 5% anchors), seeded synthetic data.  One step is
+a complete alignment with inputs resident in HBM: Phase 1 (RWR, SDDMM,
+node-cost GEMM, propagation), then OUTER outer iterations of Phase 2
+(Pass A, Pass B + Gibbs kernel) and Phase 3 (fused Sinkhorn sweeps until the
+L1 marginal error is <= 1e-4, checked every 5 sweeps), then the top-10
+read-out.  The metric is the step time (lower is better).  The Gibbs kernel
+(5 GB in BF16) is far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the 5k-node pair with the same generator
+parameters, Phase 1 plus the first outer iteration) and scales it to the
+metric's unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "50k-node time to 1e-4 marginal err, learned+BF16 vs plain FP32; sweep HBM GB/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6782.1), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_11952_gb300 import api, synth
+    from paper_2607_11952_gb300 import _lib as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    # independent replicas: rank r aligns its own pair (seed + r)
+    g = synth.config_pair(args.config, seed=synth.CONFIGS[args.config]["seed"] + rank)
+    G1, G2 = api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2)
+    params = api.Params(dtype=args.dtype)
+    al = api.Aligner(G1, G2, params, device=dev)
+    X1 = torch.from_numpy(g.X1).to(dev)
+    X2 = torch.from_numpy(g.X2).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step(aligner, record=None):
+        aligner.node_cost(X1, X2, g.anchors)
+        aligner.plan_init()
+        sweeps = 0
+        for _ in range(args.outer):
+            aligner.align_iter()
+            it, err, st = aligner.sinkhorn(args.max_sweeps, args.tol, args.check_every)
+            sweeps += it
+            if record is not None:
+                record.append((it, err, aligner.last_sweep_ms()[0]))
+        idx, score = aligner.topk(10)
+        return sweeps
+
+    al.set_timing(True)
+    for _ in range(args.warmup):
+        step(al)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = L.fa_kernel_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    rec = []
+    ev0.record(stream)
+    total_sweeps = 0
+    for _ in range(args.steps):
+        total_sweeps += step(al, rec)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = L.fa_kernel_launch_count() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    hits = al.hits_mrr(g.test_pairs)
+
+    # dominant kernel: the fused sweep; time per launch from CUDA events
+    # recorded around every sweep launch on the call's stream
+    bpe = 2 if args.dtype == "bf16" else 4
+    sweep_ms = [r[2] for r in rec if r[2] > 0]
+    sweep_w = [r[0] for r in rec]
+    avg_sweep = sum(m * w for m, w in zip(sweep_ms, sweep_w)) / max(1, sum(sweep_w))
+    algo_bytes = g.n1 * g.n2 * bpe
+    peak, peak_kind = _peaks()
+    achieved = algo_bytes / (avg_sweep * 1e-3) / 1e9 if avg_sweep > 0 else None
+    traffic = _ncu_traffic(args)
+
+    # plain FP32 cold start on the same pair, for the metric's comparison
+    fp32 = None
+    if args.compare_fp32 and args.dtype != "f32":
+        al32 = api.Aligner(G1, G2, api.Params(dtype="f32"), device=dev)
+        al32.set_timing(True)
+        step(al32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r32 = []
+        e0.record(stream)
+        sw32 = step(al32, r32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp32 = {"ms_per_step": e0.elapsed_time(e1), "sweeps": sw32,
+                "hits@1": al32.hits_mrr(g.test_pairs)["hits@1"],
+                "sweep_ms": sum(r[2] * r[0] for r in r32) / max(1, sum(r[0] for r in r32))}
+        al32.close()
+
+    # end to end through the public API from host buffers
+    e2e = _e2e(args, g, dev, api, step_fn=None) if args.e2e else None
+
+    cpu = _cpu_baseline(args) if (rank == 0 and world == 1 and args.cpu_baseline) else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(ms, 3), "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+            "data": "synthetic (seeded Chung-Lu pair; no dataset)",
+            "config": {"workload": f"{args.config}: Chung-Lu n1=n2={g.n1}, gamma=2.1, "
+                                   f"avg deg 10, 15% noise, d=128, 5% anchors; "
+                                   f"Phase 1 + {args.outer} outer x Sinkhorn to "
+                                   f"{args.tol:g} (check every {args.check_every}) + top-10",
+                       "n1": g.n1, "n2": g.n2, "outer": args.outer, "tol": args.tol,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (K is 5 GB), no flush"},
+            "sweeps_per_step": total_sweeps / args.steps,
+            "hits@1": hits["hits@1"], "mrr": hits["mrr"],
+            "plain_fp32_cold": fp32,
+            "roofline": {"kernel": "k_sweep", "bound": "hbm",
+                         "achieved": round(achieved, 1) if achieved else None,
+                         "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4) if achieved else None,
+                         "traffic": traffic, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": algo_bytes,
+                         "avg_launch_ms": round(avg_sweep, 4)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _ncu_traffic(args):
+    """DRAM bytes per k_sweep launch from the committed ncu summary, if it
+    was taken for the current kernel and dtype (None otherwise)."""
+    p = os.path.join(ROOT, "profiles", "k_sweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(args.dtype)
+    return e.get("dram_bytes_per_launch_full_size") if e else None
+
+
+def _e2e(args, g, dev, api, step_fn=None):
+    """Same step through the public API from host buffers: graph build
+    (host CSR + upload), attribute upload from pinned memory, the whole
+    alignment and the read-back of the top-10 indices."""
+    import numpy as np
+    import torch
+    X1h = torch.from_numpy(g.X1).pin_memory()
+    X2h = torch.from_numpy(g.X2).pin_memory()
+    h2d = X1h.numel() * 4 + X2h.numel() * 4 + (g.edges1.size + g.edges2.size) * 4 + g.anchors.size * 4
+    times = []
+    for k in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G1, G2 = api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2)
+        al = api.Aligner(G1, G2, api.Params(dtype=args.dtype), device=dev)
+        X1 = X1h.to(dev, non_blocking=True)
+        X2 = X2h.to(dev, non_blocking=True)
+        al.node_cost(X1, X2, g.anchors)
+        al.plan_init()
+        for _ in range(args.outer):
+            al.align_iter()
+            al.sinkhorn(args.max_sweeps, args.tol, args.check_every)
+        idx, score = al.topk(10)
+        out = idx.cpu().numpy()
+        torch.cuda.synchronize()
+        times.append((time.perf_counter() - t0) * 1e3)
+        al.close()
+        G1.close()
+        G2.close()
+    return {"value": round(min(times[1:] or times), 3), "unit": "ms",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes)}
+
+
+def _cpu_sample(args):
+    """The oracle on the 5k-node pair with the same generator parameters:
+    Phase 1 and the first outer iteration (Sinkhorn to tol), FP64."""
+    from oracle import fastalign_ref as R
+    from paper_2607_11952_gb300 import synth
+    g = synth.config_pair(args.config + "_5k" if args.config == "cl50k" else args.config, n=None)
+    p = R.Params()
+    t0 = time.perf_counter()
+    ph = R.phase1(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, p)
+    t1 = time.perf_counter()
+    R.fastalign(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, p, 1, 100000,
+                tol=args.tol, check_every=args.check_every, ph=ph)
+    t2 = time.perf_counter()
+    return g, (t1 - t0) * 1e3, (t2 - t1) * 1e3
+
+
+def _scale(args, g, t_phase1, t_outer):
+    # Phase 1 ~ n1 n2 (d + |L|) with |L| ~ n, an outer iteration ~ n1 n2;
+    # target: n = 50k, `outer` outer iterations
+    s2 = (50_000 / g.n1) * (50_000 / g.n2)
+    return t_phase1 * s2 * (50_000 / g.n1) + t_outer * s2 * args.outer
+
+
+def _cpu_baseline(args):
+    g, t_ph, t_out = _cpu_sample(args)
+    return {"value": round(_scale(args, g, t_ph, t_out), 1), "unit": "ms",
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 oracle, {g.n1}-node pair with the workload's generator "
+                      f"parameters: Phase 1 ({t_ph:.0f} ms) + first outer iteration to "
+                      f"{args.tol:g} ({t_out:.0f} ms), scaled by n^2 (outer) and n^3 "
+                      f"(Phase 1) to n=50k and {args.outer} outer iterations; "
+                      f"NumPy elementwise work is single-threaded, BLAS uses all cores"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    vals = []
+    g = None
+    for k in range(args.warmup + args.steps):
+        g, t_ph, t_out = _cpu_sample(args)
+        if k >= args.warmup:
+            vals.append(_scale(args, g, t_ph, t_out))
+    v = sum(vals) / len(vals)
+    line = {
+        "metric": METRIC, "value": round(v, 1), "unit": "ms", "impl": "reference",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: same pair generator, oracle sample at "
+                               f"n={g.n1} scaled to n=50k"},
+        "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"Phase 1 + first outer iteration at n={g.n1}, scaled"},
+        "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cl50k")
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--outer", type=int, default=30)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--check-every", type=int, default=5)
+    ap.add_argument("--max-sweeps", type=int, default=5000)
+    ap.add_argument("--no-fp32", dest="compare_fp32", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

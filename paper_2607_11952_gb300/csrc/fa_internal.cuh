@@ -48,7 +48,9 @@ extern std::atomic<int64_t> g_launches;
 enum : int { ST_NUMERIC = 1, ST_TIMEOUT = 2 };
 
 // ------------------------------------------------------------ sizes
-constexpr int64_t kLdAlign = 64;   // leading-dimension padding (elements)
+// Leading-dimension padding (elements): a multiple of 128 keeps every column
+// slab of a 16-CTA cluster a multiple of 16 bytes (TMA bulk copies).
+constexpr int64_t kLdAlign = 128;
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // ------------------------------------------------------------ device graph
@@ -129,8 +131,10 @@ fa_status launch_normalize_kernel(int n1, int n2, int64_t ld, const float* X,
                                   float* colpart, int G, cudaStream_t s);
 struct SweepPlan {
   int Q = 1;         // cluster size (column slabs per row)
+  int W = 0;         // slab width in elements (ld / Q)
   int S = 1;         // 16-byte vectors per thread per row
   int R = 1;         // rows per step
+  int NS = 2;        // shared-memory ring stages
   int G = 1;         // clusters (= rows of the partial column-sum buffer)
 };
 SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G);

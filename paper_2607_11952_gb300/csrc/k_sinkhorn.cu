@@ -11,14 +11,18 @@
 //   at the end:        v_j = nu_j / colacc_j                      (a update)
 //
 // The row sum must be complete before its column contributions are added,
-// so every CTA needs whole rows.  A row of K is split over a thread-block
-// cluster of Q CTAs: CTA q owns one column slab and keeps the matching
-// slice of v and of the column accumulators in registers for the whole
-// sweep.  Per step of R rows, each CTA reduces its slab's partial row sums,
-// pushes them into every CTA of the cluster through distributed shared
-// memory, and after one cluster barrier all CTAs hold identical row sums.
-// K is streamed with 16-byte loads that bypass L1; HBM traffic per sweep is
-// n1 x ld x sizeof(K) plus O((n1 + G ld) * 4) bytes of vectors/partials.
+// so a row is owned by one thread-block cluster of Q CTAs; CTA q owns the
+// column slab [q W, (q+1) W) and keeps the matching slice of v and of the
+// column accumulators in registers for the whole sweep.  Rows arrive through
+// a ring of NS shared-memory stages filled by TMA bulk copies (one producer
+// thread, mbarrier completion), so HBM latency is hidden by the ring depth,
+// not by registers.  Per step of R rows each CTA reduces its slab's partial
+// row sums and stores them into every CTA of the cluster (distributed shared
+// memory, st.async completing on the receiver's mbarrier, no fences); the
+// column update of a step runs one step later, so the exchange latency
+// overlaps the next step's partial sums.  With Q = 1 there is no exchange.
+// HBM traffic per sweep: n1 x ld x sizeof(K) plus O(n1 + G ld) floats for
+// the vectors and partial column sums.
 #include <cooperative_groups.h>
 #include <math.h>
 #include <stdlib.h>
@@ -51,12 +55,82 @@ template <> struct KT<__nv_bfloat16> {
   }
 };
 
-__device__ __forceinline__ uint4 ld_stream(const void* p) {
-  uint4 r;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-               : "l"(p));
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait on an mbarrier phase: false after about 2 s (the caller then
+// records ST_TIMEOUT and stops depending on that data).
+constexpr uint64_t kWaitNs = 2000000000ull;
+__device__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
+  if (mbar_try(a, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 28); ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %cluster_ctarank;" : "=r"(r));
   return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t map_cluster(uint32_t local_smem_addr, uint32_t cta) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_smem_addr), "r"(cta));
+  return r;
+}
+// 4-byte store into a peer CTA's shared memory that completes as 4
+// transaction bytes on the peer's mbarrier (no fence needed on either side).
+__device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint32_t remote_mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+                   remote_addr),
+               "r"(__float_as_uint(v)), "r"(remote_mbar)
+               : "memory");
 }
 
 // ------------------------------------------------------------ plan init
@@ -148,121 +222,212 @@ fa_status launch_normalize_kernel(int n1, int n2, int64_t ld, const float* X,
 }
 
 // ------------------------------------------------------------ fused sweep
-constexpr int kSweepThreads = 256;
-constexpr int kMaxQ = 16;
+constexpr int kNT = 512;            // threads per CTA
+constexpr int kNW = kNT / 32;       // warps per CTA
+constexpr int kMaxQ = 16;           // largest cluster
+constexpr int kNX = 4;              // exchange slots (step t uses t % kNX)
+constexpr int kMaxNS = 8;           // largest ring
+constexpr size_t kSmemBudget = 220 * 1024;
 
+// Shared memory: ring[NS][R][W] of K | full[kMaxNS] + xbar[kNX] mbarriers |
+// red[2][R][kNW] | xch[kNX][kMaxQ][R].
+//
+// Exchange protocol (Q > 1): the partial row sums of step t go to slot
+// t % kNX of every CTA of the cluster by st.async, each store completing
+// 4 transaction bytes on the receiver's xbar[t % kNX]; a receiver arms that
+// barrier for Q*R*4 bytes (its own arrival) before the step can complete
+// and re-arms it for step t + kNX once every thread has consumed step t.
+// A CTA sends step t only after it has received everybody's step t-2, by
+// which time each receiver has consumed step t-4 (the slot's previous user)
+// and re-armed it, so kNX = 4 slots never alias.  One cluster barrier after
+// the mbarrier initialisation and one before exit bracket all remote
+// traffic; every mbarrier wait is bounded.
 template <typename TK, int S, int R>
-__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(
-    const TK* __restrict__ K, int64_t ld, int n1, int n2,
+__global__ void __launch_bounds__(kNT, 1) k_sweep(
+    const TK* __restrict__ K, int64_t ld, int n1, int n2, int W, int NS,
     const float* __restrict__ log_v, float* __restrict__ log_u, float mu,
     float log_mu, float* __restrict__ colpart, int* __restrict__ status) {
   constexpr int V = KT<TK>::V;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int Q = (int)cluster.num_blocks();
-  const int q = (int)cluster.block_rank();
-  const int g = blockIdx.x / Q;          // cluster index = row group
+  extern __shared__ __align__(128) unsigned char smem[];
+  TK* ring = reinterpret_cast<TK*>(smem);
+  const size_t ring_bytes = (size_t)NS * R * W * sizeof(TK);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + ring_bytes);
+  uint64_t* xbar = full + kMaxNS;
+  float* red = reinterpret_cast<float*>(xbar + kNX);
+  float* xch = red + 2 * R * kNW;
+  __shared__ int s_timeout;
+
+  const int Q = (int)cluster_size();
+  const int q = (int)cluster_rank();
+  const int g = blockIdx.x / Q;            // cluster = row-step group
   const int G = gridDim.x / Q;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t nvec = ld / V;
-  const int64_t vbase = (int64_t)q * S * kSweepThreads + tid;
+  const int nsteps = (n1 + R - 1) / R;
+  const int T = g < nsteps ? (nsteps - 1 - g) / G + 1 : 0;   // cluster-uniform
+  const TK* Kslab = K + (int64_t)q * W;
+  const uint32_t row_bytes = (uint32_t)W * sizeof(TK);
+  const uint32_t xch_bytes = (uint32_t)(Q * R * 4);
 
-  __shared__ float red[R][kSweepThreads / 32];
-  __shared__ float xch[2][kMaxQ][R];
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&full[s]), 1);
+    for (int s = 0; s < kNX; ++s) mbar_init(smem_u32(&xbar[s]), 1);
+    fence_mbar_init();
+    s_timeout = 0;
+    if (Q > 1)
+      for (int t = 0; t < min(kNX, T); ++t) mbar_expect_tx(smem_u32(&xbar[t]), xch_bytes);
+  }
+  __syncthreads();
+  if (Q > 1) {   // every CTA's barriers exist before any remote store
+    cluster_arrive();
+    cluster_wait();
+  }
 
   float vv[S][V], acc[S][V];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    const int64_t vec = vbase + (int64_t)s * kSweepThreads;
+    const int e0 = (s * kNT + tid) * V;
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-      const int64_t col = vec * V + e;
-      vv[s][e] = (vec < nvec && col < n2) ? expf(log_v[col]) : 0.f;
+      const int64_t col = (int64_t)q * W + e0 + e;
+      vv[s][e] = (e0 < W && col < n2) ? expf(log_v[col]) : 0.f;
       acc[s][e] = 0.f;
     }
   }
 
-  int buf = 0;
-  int bad = 0;
-  for (int i0 = g * R; i0 < n1; i0 += G * R) {
-    uint4 kk[R][S];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = i0 + r;
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const int64_t vec = vbase + (int64_t)s * kSweepThreads;
-        if (row < n1 && vec < nvec)
-          kk[r][s] = ld_stream(K + (int64_t)row * ld + vec * V);
-        else
-          kk[r][s] = make_uint4(0u, 0u, 0u, 0u);
-      }
-    }
-    float p[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      float t = 0.f;
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        float f[V];
-        KT<TK>::unpack(kk[r][s], f);
-#pragma unroll
-        for (int e = 0; e < V; ++e) t += f[e] * vv[s][e];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      p[r] = t;
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) red[r][warp] = p[r];
-    }
-    __syncthreads();
-    if (tid < R) {
-      float t = 0.f;
-#pragma unroll
-      for (int w = 0; w < kSweepThreads / 32; ++w) t += red[tid][w];
-      for (int dst = 0; dst < Q; ++dst) {
-        float* rp = cluster.map_shared_rank(&xch[buf][q][tid], dst);
-        *rp = t;
-      }
-    }
-    cluster.sync();   // release the DSMEM stores, acquire the peers'
-    float u[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      float rs = 0.f;
-      for (int qq = 0; qq < Q; ++qq) rs += xch[buf][qq][r];
-      const int row = i0 + r;
-      float ur = 0.f;
-      if (row < n1) {
-        if (rs > 0.f && isfinite(rs)) {
-          ur = mu / rs;
-          if (!isfinite(ur)) { ur = 0.f; bad = 1; }
-        } else {
-          bad = 1;
-        }
-        if (q == 0 && tid == r) log_u[row] = log_mu - logf(rs);
-      }
-      u[r] = ur;
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        float f[V];
-        KT<TK>::unpack(kk[r][s], f);
-#pragma unroll
-        for (int e = 0; e < V; ++e) acc[s][e] += u[r] * f[e];
-      }
-    }
-    buf ^= 1;
+  // producer: step t goes to stage t % NS
+  int issued = 0;   // meaningful in thread 0 only
+  auto issue = [&](int t) {
+    const int stage = t % NS;
+    const int row0 = (g + t * G) * R;
+    const int nrows = min(R, n1 - row0);
+    const uint32_t mb = smem_u32(&full[stage]);
+    mbar_expect_tx(mb, (uint32_t)nrows * row_bytes);
+    for (int r = 0; r < nrows; ++r)
+      bulk_g2s(smem_u32(ring + ((size_t)stage * R + r) * W),
+               Kslab + (int64_t)(row0 + r) * ld, row_bytes, mb);
+  };
+  if (tid == 0) {
+    for (int t = 0; t < min(NS, T); ++t) issue(t);
+    issued = min(NS, T);
   }
-  if (bad && tid == 0) atomicOr(status, ST_NUMERIC);
+
+  bool dead = false;
+  for (int t = 0; t <= T; ++t) {
+    if (t < T) {
+      // -------- partial row sums of step t
+      const int stage = t % NS;
+      if (!dead && !mbar_wait_bounded(smem_u32(&full[stage]), (uint32_t)((t / NS) & 1))) {
+        atomicOr(status, ST_TIMEOUT);
+        s_timeout = 1;
+      }
+      const TK* buf = ring + (size_t)stage * R * W;
+      const int row0 = (g + t * G) * R;
+      float* rb = red + (t & 1) * R * kNW;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float p = 0.f;
+        if (row0 + r < n1) {
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            const int e0 = (s * kNT + tid) * V;
+            if (e0 < W) {
+              float f[V];
+              KT<TK>::unpack(*reinterpret_cast<const uint4*>(buf + (size_t)r * W + e0), f);
+#pragma unroll
+              for (int e = 0; e < V; ++e) p += f[e] * vv[s][e];
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (lane == 0) rb[r * kNW + warp] = p;
+      }
+      __syncthreads();
+      if (Q > 1 && tid < R) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < kNW; ++w) sum += rb[tid * kNW + w];
+        const uint32_t slot = smem_u32(xch + ((t % kNX) * kMaxQ + q) * R + tid);
+        const uint32_t bar = smem_u32(&xbar[t % kNX]);
+        for (int dst = 0; dst < Q; ++dst)
+          st_async_f32(map_cluster(slot, (uint32_t)dst), sum, map_cluster(bar, (uint32_t)dst));
+      }
+    }
+    if (t > 0) {
+      // -------- step t-1: full row sums, u, column accumulation
+      const int tp = t - 1;
+      if (Q > 1 && !dead &&
+          !mbar_wait_bounded(smem_u32(&xbar[tp % kNX]), (uint32_t)((tp / kNX) & 1))) {
+        atomicOr(status, ST_TIMEOUT);
+        s_timeout = 1;
+      }
+      const int stage = tp % NS;
+      const int row0 = (g + tp * G) * R;
+      const TK* buf = ring + (size_t)stage * R * W;
+      const float* rbp = red + (tp & 1) * R * kNW;
+      float u[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float rs = 0.f;
+        if (Q > 1) {
+          for (int qq = 0; qq < Q; ++qq) rs += xch[((tp % kNX) * kMaxQ + qq) * R + r];
+        } else {
+#pragma unroll
+          for (int w = 0; w < kNW; ++w) rs += rbp[r * kNW + w];
+        }
+        const int row = row0 + r;
+        float ur = 0.f;
+        if (row < n1) {
+          if (rs > 0.f && isfinite(rs)) {
+            ur = mu / rs;
+            if (!isfinite(ur)) { ur = 0.f; atomicOr(status, ST_NUMERIC); }
+          } else if (tid == 0) {
+            atomicOr(status, ST_NUMERIC);
+          }
+          if (q == 0 && tid == r) log_u[row] = log_mu - logf(rs);
+        }
+        u[r] = ur;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (row0 + r < n1) {
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            const int e0 = (s * kNT + tid) * V;
+            if (e0 < W) {
+              float f[V];
+              KT<TK>::unpack(*reinterpret_cast<const uint4*>(buf + (size_t)r * W + e0), f);
+#pragma unroll
+              for (int e = 0; e < V; ++e) acc[s][e] += u[r] * f[e];
+            }
+          }
+        }
+      }
+      __syncthreads();   // stage tp, red[tp & 1] and slot tp % kNX consumed
+      dead = s_timeout != 0;
+      if (tid == 0) {
+        if (Q > 1 && tp + kNX < T) mbar_expect_tx(smem_u32(&xbar[tp % kNX]), xch_bytes);
+        if (!dead && tp + NS < T) {
+          issue(tp + NS);
+          issued = tp + NS + 1;
+        }
+      }
+    }
+  }
+  // after a timeout, wait (bounded) for copies still in flight into the ring
+  if (tid == 0 && dead) {
+    for (int t = max(0, issued - NS); t < issued; ++t)
+      mbar_wait_bounded(smem_u32(&full[t % NS]), (uint32_t)((t / NS) & 1));
+  }
+  if (Q > 1) {   // no CTA leaves while a peer may still address its memory
+    cluster_arrive();
+    cluster_wait();
+  }
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    const int64_t vec = vbase + (int64_t)s * kSweepThreads;
-    if (vec < nvec) {
-      float* dst = colpart + (int64_t)g * ld + vec * V;
+    const int e0 = (s * kNT + tid) * V;
+    if (e0 < W) {
+      float* dst = colpart + (int64_t)g * ld + (int64_t)q * W + e0;
 #pragma unroll
       for (int e = 0; e < V; e += 4)
         *reinterpret_cast<float4*>(dst + e) =
@@ -271,30 +436,26 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(
   }
 }
 
-using SweepFn = void (*)(const void*, int64_t, int, int, const float*, float*,
-                         float, float, float*, int*);
-
 template <typename TK, int S, int R>
 static void* sweep_ptr() {
   return reinterpret_cast<void*>(&k_sweep<TK, S, R>);
 }
 
-// Register budget (256 threads, 2 CTAs/SM): about 2*S*V + 4*R*S + 20 <= 128.
-// Largest spill-free S per R (checked with -Xptxas -v).
-static constexpr int kSmaxF32[3] = {0, 8, 6};    // index R
-static constexpr int kSmaxBF16[3] = {0, 4, 3};
+// Largest S (16-byte vectors per thread and row) kept in registers without
+// spills at 512 threads: v and the column accumulators take 2*S*V floats.
+static constexpr int kSmaxF32 = 12;
+static constexpr int kSmaxBF16 = 6;
 
 static void* sweep_kernel(bool bf16, int S, int R) {
-#define FA_CASE_F32(SS, RR) if (!bf16 && S == SS && R == RR) return sweep_ptr<float, SS, RR>();
-#define FA_CASE_B16(SS, RR) if (bf16 && S == SS && R == RR) return sweep_ptr<__nv_bfloat16, SS, RR>();
-  FA_CASE_F32(1, 1) FA_CASE_F32(2, 1) FA_CASE_F32(3, 1) FA_CASE_F32(4, 1)
-  FA_CASE_F32(5, 1) FA_CASE_F32(6, 1) FA_CASE_F32(7, 1) FA_CASE_F32(8, 1)
-  FA_CASE_F32(1, 2) FA_CASE_F32(2, 2) FA_CASE_F32(3, 2) FA_CASE_F32(4, 2)
-  FA_CASE_F32(5, 2) FA_CASE_F32(6, 2)
-  FA_CASE_B16(1, 1) FA_CASE_B16(2, 1) FA_CASE_B16(3, 1) FA_CASE_B16(4, 1)
-  FA_CASE_B16(1, 2) FA_CASE_B16(2, 2) FA_CASE_B16(3, 2)
-#undef FA_CASE_F32
-#undef FA_CASE_B16
+#define FA_F(SS) \
+  if (!bf16 && S == SS) return R == 2 ? sweep_ptr<float, SS, 2>() : sweep_ptr<float, SS, 1>();
+#define FA_B(SS) \
+  if (bf16 && S == SS) return R == 2 ? sweep_ptr<__nv_bfloat16, SS, 2>() : sweep_ptr<__nv_bfloat16, SS, 1>();
+  FA_F(1) FA_F(2) FA_F(3) FA_F(4) FA_F(5) FA_F(6) FA_F(7) FA_F(8) FA_F(9)
+  FA_F(10) FA_F(11) FA_F(12)
+  FA_B(1) FA_B(2) FA_B(3) FA_B(4) FA_B(5) FA_B(6)
+#undef FA_F
+#undef FA_B
   return nullptr;
 }
 
@@ -304,36 +465,83 @@ static int env_int(const char* name, int dflt) {
   return atoi(v);
 }
 
+static size_t sweep_smem(const SweepPlan& sp, bool bf16) {
+  const size_t b = bf16 ? 2 : 4;
+  return (size_t)sp.NS * sp.R * sp.W * b + (size_t)(kMaxNS + kNX) * 8 +
+         (size_t)(2 * sp.R * kNW + kNX * kMaxQ * sp.R) * sizeof(float);
+}
+
+// Pick the smallest cluster whose column slab fits the register budget and
+// leaves at least 3 ring stages (2 for very wide rows); R = 2 rows per step
+// when the ring still has >= 3 stages.  FA_SWEEP_{Q,R,NS} override (tuning).
 SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   SweepPlan sp;
   sp.Q = 0;
   const int V = bf16 ? 8 : 4;
-  const int64_t nvec = ld / V;
-  const int* smax = bf16 ? kSmaxBF16 : kSmaxF32;
-  int Rwant = env_int("FA_SWEEP_R", 2);
-  if (Rwant < 1 || Rwant > 2) Rwant = 2;
-  int Qforce = env_int("FA_SWEEP_Q", 0);
-  for (int Q = 1; Q <= kMaxQ; Q *= 2) {
-    if (Qforce && Q != Qforce) continue;
-    const int S = (int)((nvec + (int64_t)Q * kSweepThreads - 1) / ((int64_t)Q * kSweepThreads));
-    int R = Rwant;
-    if (S > smax[R]) R = 1;
-    if (S <= smax[R]) {
-      sp.Q = Q;
-      sp.S = S < 1 ? 1 : S;
-      sp.R = R;
-      break;
+  const size_t b = bf16 ? 2 : 4;
+  const int smax = bf16 ? kSmaxBF16 : kSmaxF32;
+  const int Qforce = env_int("FA_SWEEP_Q", 0);
+  const int Rforce = env_int("FA_SWEEP_R", 0);
+  const int NSforce = env_int("FA_SWEEP_NS", 0);
+  for (int pass = 0; pass < 2 && sp.Q == 0; ++pass) {
+    const int min_ns = pass == 0 ? 3 : 2;
+    for (int Q = 1; Q <= kMaxQ && sp.Q == 0; Q *= 2) {
+      if (Qforce && Q != Qforce) continue;
+      if (ld % Q) continue;
+      const int64_t W = ld / Q;
+      if ((W * (int64_t)b) % 16) continue;
+      const int S = (int)((W + (int64_t)kNT * V - 1) / ((int64_t)kNT * V));
+      if (S > smax) continue;
+      for (int R = 2; R >= 1; --R) {
+        if (Rforce && R != Rforce) continue;
+        const size_t fixed = (size_t)(kMaxNS + kNX) * 8 + (size_t)(2 * R * kNW + kNX * kMaxQ * R) * 4;
+        int NS = (int)((kSmemBudget - fixed) / ((size_t)R * W * b));
+        if (NS > kMaxNS) NS = kMaxNS;
+        if (NSforce) NS = NSforce < NS ? NSforce : NS;
+        if (NS >= min_ns) {
+          sp.Q = Q;
+          sp.W = (int)W;
+          sp.S = S;
+          sp.R = R;
+          sp.NS = NS;
+          break;
+        }
+      }
     }
-    sp.Q = 0;
   }
+  if (sp.Q == 0) return sp;
   int G = env_int("FA_SWEEP_G", 0);
   if (G <= 0) G = max_G;
-  const int rows_needed = (n1 + sp.R - 1) / sp.R;
-  if (G > rows_needed) G = rows_needed;
+  const int steps = (n1 + sp.R - 1) / sp.R;
+  if (G > steps) G = steps;
   if (G > max_G) G = max_G;
   if (G < 1) G = 1;
   sp.G = G;
   return sp;
+}
+
+static cudaLaunchConfig_t sweep_config(const SweepPlan& sp, bool bf16, unsigned grid,
+                                       cudaLaunchAttribute* attr, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kNT);
+  cfg.dynamicSmemBytes = sweep_smem(sp, bf16);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)sp.Q;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+static cudaError_t prepare_sweep(void* fn, const SweepPlan& sp, bool bf16) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sweep_smem(sp, bf16));
+  if (e != cudaSuccess) return e;
+  if (sp.Q > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
 }
 
 fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
@@ -341,7 +549,7 @@ fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
                        float* log_u, float mu, float* colpart, int* status,
                        cudaStream_t s) {
   if (sp.Q < 1) {
-    set_error("fa_sinkhorn: n2=%d too wide for a %d-CTA cluster sweep", n2, kMaxQ);
+    set_error("fa_sinkhorn: no cluster shape fits a row of %lld elements", (long long)ld);
     return FA_ERR_UNSUPPORTED;
   }
   void* fn = sweep_kernel(bf16, sp.S, sp.R);
@@ -349,33 +557,22 @@ fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
     set_error("fa_sinkhorn: no sweep kernel for S=%d R=%d", sp.S, sp.R);
     return FA_ERR_UNSUPPORTED;
   }
-  if (sp.Q > 8) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) {
-      set_error("cluster size %d not allowed: %s", sp.Q, cudaGetErrorString(e));
-      return FA_ERR_UNSUPPORTED;
-    }
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(sp.G * sp.Q));
-  cfg.blockDim = dim3(kSweepThreads);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)sp.Q;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  const float log_mu = logf(mu);
-  void* args[] = {(void*)&K, (void*)&ld, (void*)&n1, (void*)&n2,
-                  (void*)&log_v, (void*)&log_u, (void*)&mu, (void*)&log_mu,
-                  (void*)&colpart, (void*)&status};
-  cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+  cudaError_t e = prepare_sweep(fn, sp, bf16);
   if (e != cudaSuccess) {
-    set_error("k_sweep launch (Q=%d S=%d R=%d G=%d): %s", sp.Q, sp.S, sp.R,
-              sp.G, cudaGetErrorString(e));
+    set_error("k_sweep attributes: %s", cudaGetErrorString(e));
+    return FA_ERR_UNSUPPORTED;
+  }
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = sweep_config(sp, bf16, (unsigned)(sp.G * sp.Q), attr, s);
+  const float log_mu = logf(mu);
+  int W = sp.W, NS = sp.NS;
+  void* args[] = {(void*)&K, (void*)&ld, (void*)&n1, (void*)&n2, (void*)&W,
+                  (void*)&NS, (void*)&log_v, (void*)&log_u, (void*)&mu,
+                  (void*)&log_mu, (void*)&colpart, (void*)&status};
+  e = cudaLaunchKernelExC(&cfg, fn, args);
+  if (e != cudaSuccess) {
+    set_error("k_sweep launch (Q=%d S=%d R=%d NS=%d G=%d): %s", sp.Q, sp.S, sp.R,
+              sp.NS, sp.G, cudaGetErrorString(e));
     return FA_ERR_CUDA;
   }
   FA_LAUNCHED("k_sweep");
@@ -386,17 +583,12 @@ fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
 int sweep_max_active_clusters(const SweepPlan& sp, bool bf16) {
   void* fn = sweep_kernel(bf16, sp.S, sp.R);
   if (!fn || sp.Q < 1) return 0;
-  if (sp.Q > 8) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(sp.Q * 64));
-  cfg.blockDim = dim3(kSweepThreads);
+  if (prepare_sweep(fn, sp, bf16) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)sp.Q;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cudaLaunchConfig_t cfg = sweep_config(sp, bf16, (unsigned)(sp.Q * 64), attr, 0);
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
     cudaGetLastError();
