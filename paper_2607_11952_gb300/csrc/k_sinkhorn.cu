@@ -44,16 +44,25 @@ template <> struct KT<float> {
 };
 template <> struct KT<__nv_bfloat16> {
   static constexpr int V = 8;
+  // bf16 is the upper half of an fp32: widen by shifting, register-only.
   __device__ static __forceinline__ void unpack(const uint4& u, float (&f)[8]) {
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float2 t = __bfloat1622float2(h[q]);
-      f[2 * q] = t.x;
-      f[2 * q + 1] = t.y;
+      f[2 * q] = __uint_as_float(w[q] << 16);
+      f[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
     }
   }
 };
+
+// One 16-byte shared-memory load (a single LDS.128 per thread).
+__device__ __forceinline__ uint4 lds128(const void* p) {
+  uint4 r;
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+  return r;
+}
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -323,24 +332,34 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
       const TK* buf = ring + (size_t)stage * R * W;
       const int row0 = (g + t * G) * R;
       float* rb = red + (t & 1) * R * kNW;
+      // four independent accumulators per row keep the FMA chains short;
+      // the R rows' shuffle trees are interleaved
+      float p[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float p = 0.f;
+        float pa[4] = {0.f, 0.f, 0.f, 0.f};
         if (row0 + r < n1) {
 #pragma unroll
           for (int s = 0; s < S; ++s) {
             const int e0 = (s * kNT + tid) * V;
             if (e0 < W) {
               float f[V];
-              KT<TK>::unpack(*reinterpret_cast<const uint4*>(buf + (size_t)r * W + e0), f);
+              KT<TK>::unpack(lds128(buf + (size_t)r * W + e0), f);
 #pragma unroll
-              for (int e = 0; e < V; ++e) p += f[e] * vv[s][e];
+              for (int e = 0; e < V; ++e) pa[e & 3] = fmaf(f[e], vv[s][e], pa[e & 3]);
             }
           }
         }
+        p[r] = (pa[0] + pa[1]) + (pa[2] + pa[3]);
+      }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-        if (lane == 0) rb[r * kNW + warp] = p;
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r] += __shfl_xor_sync(0xffffffffu, p[r], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) rb[r * kNW + warp] = p[r];
       }
       __syncthreads();
       if (Q > 1 && tid < R) {
@@ -396,7 +415,7 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
             const int e0 = (s * kNT + tid) * V;
             if (e0 < W) {
               float f[V];
-              KT<TK>::unpack(*reinterpret_cast<const uint4*>(buf + (size_t)r * W + e0), f);
+              KT<TK>::unpack(lds128(buf + (size_t)r * W + e0), f);
 #pragma unroll
               for (int e = 0; e < V; ++e) acc[s][e] += u[r] * f[e];
             }
@@ -450,7 +469,9 @@ static void* sweep_kernel(bool bf16, int S, int R) {
 #define FA_F(SS) \
   if (!bf16 && S == SS) return R == 2 ? sweep_ptr<float, SS, 2>() : sweep_ptr<float, SS, 1>();
 #define FA_B(SS) \
-  if (bf16 && S == SS) return R == 2 ? sweep_ptr<__nv_bfloat16, SS, 2>() : sweep_ptr<__nv_bfloat16, SS, 1>();
+  if (bf16 && S == SS)                                                         \
+    return R == 4 ? sweep_ptr<__nv_bfloat16, SS, 4>()                          \
+                  : R == 2 ? sweep_ptr<__nv_bfloat16, SS, 2>() : sweep_ptr<__nv_bfloat16, SS, 1>();
   FA_F(1) FA_F(2) FA_F(3) FA_F(4) FA_F(5) FA_F(6) FA_F(7) FA_F(8) FA_F(9)
   FA_F(10) FA_F(11) FA_F(12)
   FA_B(1) FA_B(2) FA_B(3) FA_B(4) FA_B(5) FA_B(6)
@@ -492,7 +513,7 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
       if ((W * (int64_t)b) % 16) continue;
       const int S = (int)((W + (int64_t)kNT * V - 1) / ((int64_t)kNT * V));
       if (S > smax) continue;
-      for (int R = 2; R >= 1; --R) {
+      for (int R = bf16 ? 4 : 2; R >= 1; R /= 2) {
         if (Rforce && R != Rforce) continue;
         const size_t fixed = (size_t)(kMaxNS + kNX) * 8 + (size_t)(2 * R * kNW + kNX * kMaxQ * R) * 4;
         int NS = (int)((kSmemBudget - fixed) / ((size_t)R * W * b));
