@@ -135,6 +135,7 @@ struct SweepPlan {
   int S = 1;         // 16-byte vectors per thread per row
   int R = 1;         // rows per step
   int NS = 2;        // shared-memory ring stages
+  int NT = 512;      // threads per CTA (256: two CTAs per SM)
   int G = 1;         // clusters (= rows of the partial column-sum buffer)
 };
 SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G);

@@ -55,6 +55,42 @@ template <> struct KT<__nv_bfloat16> {
   }
 };
 
+// Packed pairs of fp32 in one 64-bit register pair, for the paired FMA of
+// sm_100+ (fma.rn.f32x2): one instruction per two elements.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t pk2(float lo, float hi) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ f2_t pk2u(uint32_t lo, uint32_t hi) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(f2_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ f2_t ffma2(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// the 16 bytes of K as V/2 packed fp32 pairs (columns 2k, 2k+1)
+__device__ __forceinline__ void pairs(const uint4& u, f2_t (&p)[2], float) {
+  p[0] = pk2u(u.x, u.y);
+  p[1] = pk2u(u.z, u.w);
+}
+__device__ __forceinline__ void pairs(const uint4& u, f2_t (&p)[4], __nv_bfloat16) {
+  // bf16 is the upper half of an fp32: widen by shift / mask
+  p[0] = pk2u(u.x << 16, u.x & 0xffff0000u);
+  p[1] = pk2u(u.y << 16, u.y & 0xffff0000u);
+  p[2] = pk2u(u.z << 16, u.z & 0xffff0000u);
+  p[3] = pk2u(u.w << 16, u.w & 0xffff0000u);
+}
+
 // One 16-byte shared-memory load (a single LDS.128 per thread).
 __device__ __forceinline__ uint4 lds128(const void* p) {
   uint4 r;
@@ -231,8 +267,8 @@ fa_status launch_normalize_kernel(int n1, int n2, int64_t ld, const float* X,
 }
 
 // ------------------------------------------------------------ fused sweep
-constexpr int kNT = 512;            // threads per CTA
-constexpr int kNW = kNT / 32;       // warps per CTA
+
+
 constexpr int kMaxQ = 16;           // largest cluster
 constexpr int kNX = 4;              // exchange slots (step t uses t % kNX)
 constexpr int kMaxNS = 8;           // largest ring
@@ -251,19 +287,20 @@ constexpr size_t kSmemBudget = 220 * 1024;
 // and re-armed it, so kNX = 4 slots never alias.  One cluster barrier after
 // the mbarrier initialisation and one before exit bracket all remote
 // traffic; every mbarrier wait is bounded.
-template <typename TK, int S, int R>
-__global__ void __launch_bounds__(kNT, 1) k_sweep(
+template <typename TK, int S, int R, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k_sweep(
     const TK* __restrict__ K, int64_t ld, int n1, int n2, int W, int NS,
     const float* __restrict__ log_v, float* __restrict__ log_u, float mu,
     float log_mu, float* __restrict__ colpart, int* __restrict__ status) {
   constexpr int V = KT<TK>::V;
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem[];
   TK* ring = reinterpret_cast<TK*>(smem);
   const size_t ring_bytes = (size_t)NS * R * W * sizeof(TK);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + ring_bytes);
   uint64_t* xbar = full + kMaxNS;
   float* red = reinterpret_cast<float*>(xbar + kNX);
-  float* xch = red + 2 * R * kNW;
+  float* xch = red + 2 * R * NW;
   __shared__ int s_timeout;
 
   const int Q = (int)cluster_size();
@@ -291,15 +328,19 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
     cluster_wait();
   }
 
-  float vv[S][V], acc[S][V];
+  // v and the column accumulators as packed pairs (columns 2k, 2k+1)
+  constexpr int V2 = V / 2;
+  f2_t vv[S][V2], acc[S][V2];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    const int e0 = (s * kNT + tid) * V;
+    const int e0 = (s * NT + tid) * V;
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
-      const int64_t col = (int64_t)q * W + e0 + e;
-      vv[s][e] = (e0 < W && col < n2) ? expf(log_v[col]) : 0.f;
-      acc[s][e] = 0.f;
+    for (int k = 0; k < V2; ++k) {
+      const int64_t col = (int64_t)q * W + e0 + 2 * k;
+      const float a = (e0 < W && col < n2) ? expf(log_v[col]) : 0.f;
+      const float b = (e0 < W && col + 1 < n2) ? expf(log_v[col + 1]) : 0.f;
+      vv[s][k] = pk2(a, b);
+      acc[s][k] = pk2(0.f, 0.f);
     }
   }
 
@@ -331,26 +372,27 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
       }
       const TK* buf = ring + (size_t)stage * R * W;
       const int row0 = (g + t * G) * R;
-      float* rb = red + (t & 1) * R * kNW;
-      // four independent accumulators per row keep the FMA chains short;
-      // the R rows' shuffle trees are interleaved
+      float* rb = red + (t & 1) * R * NW;
+      // two independent paired accumulators per row (four FMA chains); the
+      // R rows' shuffle trees are interleaved
       float p[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float pa[4] = {0.f, 0.f, 0.f, 0.f};
+        f2_t pa[2] = {pk2(0.f, 0.f), pk2(0.f, 0.f)};
         if (row0 + r < n1) {
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const int e0 = (s * kNT + tid) * V;
+            const int e0 = (s * NT + tid) * V;
             if (e0 < W) {
-              float f[V];
-              KT<TK>::unpack(lds128(buf + (size_t)r * W + e0), f);
+              f2_t f[V2];
+              pairs(lds128(buf + (size_t)r * W + e0), f, TK());
 #pragma unroll
-              for (int e = 0; e < V; ++e) pa[e & 3] = fmaf(f[e], vv[s][e], pa[e & 3]);
+              for (int k = 0; k < V2; ++k) pa[k & 1] = ffma2(f[k], vv[s][k], pa[k & 1]);
             }
           }
         }
-        p[r] = (pa[0] + pa[1]) + (pa[2] + pa[3]);
+        const float2 a = upk2(pa[0]), b = upk2(pa[1]);
+        p[r] = (a.x + a.y) + (b.x + b.y);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -359,13 +401,13 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
       }
       if (lane == 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) rb[r * kNW + warp] = p[r];
+        for (int r = 0; r < R; ++r) rb[r * NW + warp] = p[r];
       }
       __syncthreads();
       if (Q > 1 && tid < R) {
         float sum = 0.f;
 #pragma unroll
-        for (int w = 0; w < kNW; ++w) sum += rb[tid * kNW + w];
+        for (int w = 0; w < NW; ++w) sum += rb[tid * NW + w];
         const uint32_t slot = smem_u32(xch + ((t % kNX) * kMaxQ + q) * R + tid);
         const uint32_t bar = smem_u32(&xbar[t % kNX]);
         for (int dst = 0; dst < Q; ++dst)
@@ -383,7 +425,7 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
       const int stage = tp % NS;
       const int row0 = (g + tp * G) * R;
       const TK* buf = ring + (size_t)stage * R * W;
-      const float* rbp = red + (tp & 1) * R * kNW;
+      const float* rbp = red + (tp & 1) * R * NW;
       float u[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -392,13 +434,13 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
           for (int qq = 0; qq < Q; ++qq) rs += xch[((tp % kNX) * kMaxQ + qq) * R + r];
         } else {
 #pragma unroll
-          for (int w = 0; w < kNW; ++w) rs += rbp[r * kNW + w];
+          for (int w = 0; w < NW; ++w) rs += rbp[r * NW + w];
         }
         const int row = row0 + r;
         float ur = 0.f;
         if (row < n1) {
           if (rs > 0.f && isfinite(rs)) {
-            ur = mu / rs;
+            ur = __fdividef(mu, rs);   // identical in every CTA of the cluster
             if (!isfinite(ur)) { ur = 0.f; atomicOr(status, ST_NUMERIC); }
           } else if (tid == 0) {
             atomicOr(status, ST_NUMERIC);
@@ -410,14 +452,15 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (row0 + r < n1) {
+          const f2_t u2 = pk2(u[r], u[r]);
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const int e0 = (s * kNT + tid) * V;
+            const int e0 = (s * NT + tid) * V;
             if (e0 < W) {
-              float f[V];
-              KT<TK>::unpack(lds128(buf + (size_t)r * W + e0), f);
+              f2_t f[V2];
+              pairs(lds128(buf + (size_t)r * W + e0), f, TK());
 #pragma unroll
-              for (int e = 0; e < V; ++e) acc[s][e] += u[r] * f[e];
+              for (int k = 0; k < V2; ++k) acc[s][k] = ffma2(u2, f[k], acc[s][k]);
             }
           }
         }
@@ -444,20 +487,28 @@ __global__ void __launch_bounds__(kNT, 1) k_sweep(
   }
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    const int e0 = (s * kNT + tid) * V;
+    const int e0 = (s * NT + tid) * V;
     if (e0 < W) {
       float* dst = colpart + (int64_t)g * ld + (int64_t)q * W + e0;
 #pragma unroll
-      for (int e = 0; e < V; e += 4)
-        *reinterpret_cast<float4*>(dst + e) =
-            make_float4(acc[s][e], acc[s][e + 1], acc[s][e + 2], acc[s][e + 3]);
+      for (int k = 0; k < V2; k += 2) {
+        const float2 a = upk2(acc[s][k]), b = upk2(acc[s][k + 1]);
+        *reinterpret_cast<float4*>(dst + 2 * k) = make_float4(a.x, a.y, b.x, b.y);
+      }
     }
   }
 }
 
 template <typename TK, int S, int R>
-static void* sweep_ptr() {
-  return reinterpret_cast<void*>(&k_sweep<TK, S, R>);
+static void* sweep_ptr(int NT) {
+  if (NT == 1024) {   // 64 registers per thread: only small slabs per thread
+    if constexpr (S <= (sizeof(TK) == 2 ? 3 : 6))
+      return reinterpret_cast<void*>(&k_sweep<TK, S, R, 1024>);
+    else
+      return nullptr;
+  }
+  return NT == 256 ? reinterpret_cast<void*>(&k_sweep<TK, S, R, 256>)
+                   : reinterpret_cast<void*>(&k_sweep<TK, S, R, 512>);
 }
 
 // Largest S (16-byte vectors per thread and row) kept in registers without
@@ -465,13 +516,13 @@ static void* sweep_ptr() {
 static constexpr int kSmaxF32 = 12;
 static constexpr int kSmaxBF16 = 6;
 
-static void* sweep_kernel(bool bf16, int S, int R) {
+static void* sweep_kernel(bool bf16, int S, int R, int NT) {
 #define FA_F(SS) \
-  if (!bf16 && S == SS) return R == 2 ? sweep_ptr<float, SS, 2>() : sweep_ptr<float, SS, 1>();
+  if (!bf16 && S == SS) return R == 2 ? sweep_ptr<float, SS, 2>(NT) : sweep_ptr<float, SS, 1>(NT);
 #define FA_B(SS) \
   if (bf16 && S == SS)                                                         \
-    return R == 4 ? sweep_ptr<__nv_bfloat16, SS, 4>()                          \
-                  : R == 2 ? sweep_ptr<__nv_bfloat16, SS, 2>() : sweep_ptr<__nv_bfloat16, SS, 1>();
+    return R == 4 ? sweep_ptr<__nv_bfloat16, SS, 4>(NT)                        \
+                  : R == 2 ? sweep_ptr<__nv_bfloat16, SS, 2>(NT) : sweep_ptr<__nv_bfloat16, SS, 1>(NT);
   FA_F(1) FA_F(2) FA_F(3) FA_F(4) FA_F(5) FA_F(6) FA_F(7) FA_F(8) FA_F(9)
   FA_F(10) FA_F(11) FA_F(12)
   FA_B(1) FA_B(2) FA_B(3) FA_B(4) FA_B(5) FA_B(6)
@@ -489,7 +540,7 @@ static int env_int(const char* name, int dflt) {
 static size_t sweep_smem(const SweepPlan& sp, bool bf16) {
   const size_t b = bf16 ? 2 : 4;
   return (size_t)sp.NS * sp.R * sp.W * b + (size_t)(kMaxNS + kNX) * 8 +
-         (size_t)(2 * sp.R * kNW + kNX * kMaxQ * sp.R) * sizeof(float);
+         (size_t)(2 * sp.R * (sp.NT / 32) + kNX * kMaxQ * sp.R) * sizeof(float);
 }
 
 // Pick the smallest cluster whose column slab fits the register budget and
@@ -500,10 +551,17 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   sp.Q = 0;
   const int V = bf16 ? 8 : 4;
   const size_t b = bf16 ? 2 : 4;
-  const int smax = bf16 ? kSmaxBF16 : kSmaxF32;
   const int Qforce = env_int("FA_SWEEP_Q", 0);
   const int Rforce = env_int("FA_SWEEP_R", 0);
   const int NSforce = env_int("FA_SWEEP_NS", 0);
+  // 512 threads and one CTA per SM, or 256 threads and two CTAs per SM
+  // (half the shared memory each)
+  // measured on GB300 (10k and 50k rows, FP32 and BF16): 256 threads with two
+  // CTAs per SM is as fast or faster than 512 (one CTA) and 1024 threads
+  const int nt_env = env_int("FA_SWEEP_NT", 256);
+  const int NT = (nt_env == 256 || nt_env == 1024) ? nt_env : 512;
+  const int smax = NT == 1024 ? (bf16 ? 3 : 6) : (bf16 ? kSmaxBF16 : kSmaxF32);
+  const size_t budget = NT == 256 ? kSmemBudget / 2 : kSmemBudget;
   for (int pass = 0; pass < 2 && sp.Q == 0; ++pass) {
     const int min_ns = pass == 0 ? 3 : 2;
     for (int Q = 1; Q <= kMaxQ && sp.Q == 0; Q *= 2) {
@@ -511,12 +569,12 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
       if (ld % Q) continue;
       const int64_t W = ld / Q;
       if ((W * (int64_t)b) % 16) continue;
-      const int S = (int)((W + (int64_t)kNT * V - 1) / ((int64_t)kNT * V));
+      const int S = (int)((W + (int64_t)NT * V - 1) / ((int64_t)NT * V));
       if (S > smax) continue;
       for (int R = bf16 ? 4 : 2; R >= 1; R /= 2) {
         if (Rforce && R != Rforce) continue;
-        const size_t fixed = (size_t)(kMaxNS + kNX) * 8 + (size_t)(2 * R * kNW + kNX * kMaxQ * R) * 4;
-        int NS = (int)((kSmemBudget - fixed) / ((size_t)R * W * b));
+        const size_t fixed = (size_t)(kMaxNS + kNX) * 8 + (size_t)(2 * R * (NT / 32) + kNX * kMaxQ * R) * 4;
+        int NS = (int)((budget - fixed) / ((size_t)R * W * b));
         if (NS > kMaxNS) NS = kMaxNS;
         if (NSforce) NS = NSforce < NS ? NSforce : NS;
         if (NS >= min_ns) {
@@ -525,6 +583,7 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
           sp.S = S;
           sp.R = R;
           sp.NS = NS;
+          sp.NT = NT;
           break;
         }
       }
@@ -545,7 +604,7 @@ static cudaLaunchConfig_t sweep_config(const SweepPlan& sp, bool bf16, unsigned 
                                        cudaLaunchAttribute* attr, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kNT);
+  cfg.blockDim = dim3((unsigned)sp.NT);
   cfg.dynamicSmemBytes = sweep_smem(sp, bf16);
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -573,7 +632,7 @@ fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
     set_error("fa_sinkhorn: no cluster shape fits a row of %lld elements", (long long)ld);
     return FA_ERR_UNSUPPORTED;
   }
-  void* fn = sweep_kernel(bf16, sp.S, sp.R);
+  void* fn = sweep_kernel(bf16, sp.S, sp.R, sp.NT);
   if (!fn) {
     set_error("fa_sinkhorn: no sweep kernel for S=%d R=%d", sp.S, sp.R);
     return FA_ERR_UNSUPPORTED;
@@ -602,7 +661,7 @@ fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
 
 // Number of clusters of the chosen shape that fit on the device at once.
 int sweep_max_active_clusters(const SweepPlan& sp, bool bf16) {
-  void* fn = sweep_kernel(bf16, sp.S, sp.R);
+  void* fn = sweep_kernel(bf16, sp.S, sp.R, sp.NT);
   if (!fn || sp.Q < 1) return 0;
   if (prepare_sweep(fn, sp, bf16) != cudaSuccess) {
     cudaGetLastError();
