@@ -1,0 +1,62 @@
+"""Pins for the FP64 oracle of the learned warm start: analytic gradients
+against central finite differences, gauge invariance, a hand-sized forward
+pass and the Adam closed form for a constant gradient.  CPU only."""
+import numpy as np
+
+from oracle import fastalign_ref as R
+from oracle import gnn_ref as G
+from paper_2607_11952_gb300 import synth
+
+
+def _setup(n=40, seed=0):
+    rng = np.random.default_rng(seed)
+    e = synth.erdos_renyi(n, 3.0, synth.rng_for(seed))
+    A = R.row_normalized(n, e)
+    F = rng.standard_normal((n, G.FIN))
+    y = rng.standard_normal(n)
+    theta = 0.3 * rng.standard_normal(G.N_PARAMS)
+    return A, F, y, theta
+
+
+def test_gradient_matches_central_differences():
+    A, F, y, theta = _setup()
+    L, g = G.backward(A, F, theta, y)
+    h = 1e-6
+    num = np.empty_like(theta)
+    for k in range(theta.size):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        num[k] = (G.loss(G.forward(A, F, tp)[0], y) - G.loss(G.forward(A, F, tm)[0], y)) / (2 * h)
+    np.testing.assert_allclose(g, num, rtol=1e-5, atol=1e-8)
+    assert abs(g[-1]) < 1e-12          # the bias c does not change a centred loss
+
+
+def test_loss_is_gauge_invariant():
+    A, F, y, theta = _setup(seed=1)
+    a, _ = G.forward(A, F, theta)
+    assert abs(G.loss(a, y) - G.loss(a + 3.7, y - 1.2)) < 1e-12
+
+
+def test_forward_hand_example():
+    # path 0-1-2; W1 picks feature 0 into unit 0; w2 = e_0; c = 0.5
+    A = R.row_normalized(3, np.array([[0, 1], [1, 2]]))
+    F = np.array([[1.0, 0, 0], [-2.0, 0, 0], [3.0, 0, 0]])
+    theta = np.zeros(G.N_PARAMS)
+    theta[0] = 1.0                       # W1[0, 0]
+    theta[G.FIN * G.HIDDEN + G.HIDDEN] = 1.0   # w2[0]
+    theta[-1] = 0.5
+    a, c = G.forward(A, F, theta)
+    # AF[:,0] = (-2, 2, -2); relu -> (0, 2, 0); a = Abar z2 + .5 = (2.5, .5, 2.5)
+    np.testing.assert_allclose(a, [2.5, 0.5, 2.5])
+
+
+def test_adam_constant_gradient_closed_form():
+    theta = np.zeros(4)
+    m = np.zeros(4)
+    v = np.zeros(4)
+    g = np.array([1.0, -2.0, 0.5, 0.0])
+    for t in range(1, 6):
+        theta, m, v = G.adam_step(theta, m, v, g, t, lr=0.1)
+    # with a constant gradient the bias-corrected step is lr * sign(g)
+    np.testing.assert_allclose(theta, -0.5 * np.sign(g) * (g != 0), atol=1e-7)
