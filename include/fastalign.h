@@ -201,6 +201,65 @@ fa_status fa_rank(fa_ctx* ctx, const void* K, const float* log_v,
 fa_status fa_ctx_set_timing(fa_ctx* ctx, int32_t on);
 fa_status fa_ctx_last_sweep_ms(const fa_ctx* ctx, double* ms, int32_t* n);
 
+/* ======================================================================
+ * Learned warm start of the Sinkhorn solves.  The paper has no learned
+ * component: this is a small 2-layer graph network on the column graph
+ * G2 (hidden width 64, BF16 weights, FP32 accumulation) that predicts the
+ * correction y = log v* - log v1 between the converged column scaling of a
+ * solve and its cold first column update, so that fa_sinkhorn can start
+ * from warm_log_v = log v1 + prediction.
+ *
+ *   AF = Abar F,  A1 = AF W1 + b1,  H = relu(A1),  z2 = H w2,
+ *   a  = Abar z2 + c,
+ *   L  = 1/n sum_j ((a_j - mean a) - (y_j - mean y))^2   (gauge invariant)
+ *
+ * Parameters (FP32 master copy, FA_GNN_NPARAMS floats): W1 [3 x 64,
+ * row-major] | b1 [64] | w2 [64] | c.  The forward pass reads BF16 copies
+ * of W1 and w2 refreshed by fa_gnn_set_params and fa_gnn_adam_step.
+ * ====================================================================== */
+#define FA_GNN_FIN 3
+#define FA_GNN_HIDDEN 64
+#define FA_GNN_NPARAMS (FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1)
+
+typedef struct fa_gnn fa_gnn;
+
+/* A model with all parameters and the Adam state set to zero. */
+fa_status fa_gnn_create(fa_gnn** out);
+fa_status fa_gnn_destroy(fa_gnn* g);
+/* host_theta: FA_GNN_NPARAMS floats (host).  Resets the Adam state.
+ * Synchronous. */
+fa_status fa_gnn_set_params(fa_gnn* g, const float* host_theta);
+fa_status fa_gnn_get_params(const fa_gnn* g, float* host_theta);
+/* Floats of caller-owned device workspace the calls below need for a
+ * graph of n nodes (activations kept for the backward pass, partial sums);
+ * -1 if n < 1. */
+int64_t fa_gnn_workspace_floats(int32_t n);
+
+/* Per-node inputs F (device, n x 3 row-major) of the column graph g2:
+ * (log_v1_j - mean log_v1, corr_prev_j, log(1 + deg_j)); corr_prev
+ * (device, n, nullable = zeros) is the previous solve's correction.
+ * ws: workspace of fa_gnn_workspace_floats(n). */
+fa_status fa_gnn_features(const fa_graph* g2, const float* log_v1,
+                          const float* corr_prev, float* F, float* ws,
+                          fa_stream_t stream);
+/* a_out (device, n) = model(F) on graph g; keeps activations in ws. */
+fa_status fa_gnn_forward(fa_gnn* m, const fa_graph* g, const float* F,
+                         float* ws, float* a_out, fa_stream_t stream);
+/* Gradient of L for the forward pass whose activations ws holds.
+ * grad: device, FA_GNN_NPARAMS floats (overwritten); loss: device scalar
+ * (nullable). */
+fa_status fa_gnn_backward(fa_gnn* m, const fa_graph* g, const float* ws,
+                          const float* a_pred, const float* target,
+                          float* grad, float* loss, fa_stream_t stream);
+/* One Adam step (bias-corrected) of the FP32 master parameters with the
+ * device gradient grad; refreshes the BF16 copies. */
+fa_status fa_gnn_adam_step(fa_gnn* m, const float* grad, float lr,
+                           float beta1, float beta2, float eps,
+                           fa_stream_t stream);
+/* out = a x + b y on device vectors of n floats (y nullable = 0). */
+fa_status fa_vec_axpby(int32_t n, float a, const float* x, float b,
+                       const float* y, float* out, fa_stream_t stream);
+
 /* Per-thread description of the last error. */
 const char* fa_last_error_string(void);
 

@@ -77,7 +77,20 @@ SIGNATURES = {
     "fa_ctx_last_sweep_ms": (_i32, [_p, ctypes.POINTER(_f64), ctypes.POINTER(_i32)]),
     "fa_last_error_string": (ctypes.c_char_p, []),
     "fa_kernel_launch_count": (_i64, []),
+    "fa_gnn_create": (_i32, [ctypes.POINTER(_p)]),
+    "fa_gnn_destroy": (_i32, [_p]),
+    "fa_gnn_set_params": (_i32, [_p, _p]),
+    "fa_gnn_get_params": (_i32, [_p, _p]),
+    "fa_gnn_workspace_floats": (_i64, [_i32]),
+    "fa_gnn_features": (_i32, [_p, _p, _p, _p, _p, _p]),
+    "fa_gnn_forward": (_i32, [_p, _p, _p, _p, _p, _p]),
+    "fa_gnn_backward": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p]),
+    "fa_gnn_adam_step": (_i32, [_p, _p, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, _p]),
+    "fa_vec_axpby": (_i32, [_i32, ctypes.c_float, _p, ctypes.c_float, _p, _p, _p]),
 }
+FA_GNN_FIN, FA_GNN_HIDDEN = 3, 64
+FA_GNN_NPARAMS = FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1
 
 _lib = None
 
@@ -232,3 +245,57 @@ def fa_last_error_string() -> str:
 
 def fa_kernel_launch_count() -> int:
     return lib().fa_kernel_launch_count()
+
+
+# ------------------------------------------------------------ learned warm start
+
+def fa_gnn_create() -> int:
+    out = _p()
+    _check(lib().fa_gnn_create(ctypes.byref(out)), "fa_gnn_create")
+    return out.value
+
+
+def fa_gnn_destroy(m: int) -> None:
+    _check(lib().fa_gnn_destroy(m), "fa_gnn_destroy")
+
+
+def fa_gnn_set_params(m: int, theta: np.ndarray) -> None:
+    t = np.ascontiguousarray(theta, dtype=np.float32)
+    if t.size != FA_GNN_NPARAMS:
+        raise ValueError(f"expected {FA_GNN_NPARAMS} parameters")
+    _check(lib().fa_gnn_set_params(m, ptr(t)), "fa_gnn_set_params")
+
+
+def fa_gnn_get_params(m: int) -> np.ndarray:
+    t = np.empty(FA_GNN_NPARAMS, np.float32)
+    _check(lib().fa_gnn_get_params(m, ptr(t)), "fa_gnn_get_params")
+    return t
+
+
+def fa_gnn_workspace_floats(n: int) -> int:
+    return lib().fa_gnn_workspace_floats(n)
+
+
+def fa_gnn_features(g2, log_v1, corr_prev, F, ws, stream=None) -> None:
+    _check(lib().fa_gnn_features(g2, ptr(log_v1), ptr(corr_prev), ptr(F), ptr(ws),
+                                 stream_ptr(stream)), "fa_gnn_features")
+
+
+def fa_gnn_forward(m, g, F, ws, a_out, stream=None) -> None:
+    _check(lib().fa_gnn_forward(m, g, ptr(F), ptr(ws), ptr(a_out), stream_ptr(stream)),
+           "fa_gnn_forward")
+
+
+def fa_gnn_backward(m, g, ws, a_pred, target, grad, loss, stream=None) -> None:
+    _check(lib().fa_gnn_backward(m, g, ptr(ws), ptr(a_pred), ptr(target), ptr(grad),
+                                 ptr(loss), stream_ptr(stream)), "fa_gnn_backward")
+
+
+def fa_gnn_adam_step(m, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+    _check(lib().fa_gnn_adam_step(m, ptr(grad), float(lr), float(beta1), float(beta2),
+                                  float(eps), stream_ptr(stream)), "fa_gnn_adam_step")
+
+
+def fa_vec_axpby(n, a, x, b, y, out, stream=None) -> None:
+    _check(lib().fa_vec_axpby(int(n), float(a), ptr(x), float(b), ptr(y), ptr(out),
+                              stream_ptr(stream)), "fa_vec_axpby")

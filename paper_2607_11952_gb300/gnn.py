@@ -1,0 +1,200 @@
+"""Learned warm start of the Sinkhorn solves (not part of the paper).
+
+A 2-layer graph network on the column graph G2 (hidden width 64, BF16
+weights) predicts, for the solve of one outer iteration, the correction
+y = log v* - log v1 between the converged column scaling v* and the cold
+first column update v1 that fa_align_iter leaves in ``log_v``.  The solve
+then starts from ``warm_log_v = log v1 + prediction``; the plain cold start
+(no warm start) stays available and is the reference the model is judged
+against.  The model's forward, backward and Adam kernels are the library's
+(fa_gnn_*); this module only moves tensors and decides what to call.
+
+Training data are the method's own solves: Chung-Lu pairs with n uniform in
+[2000, 5000], degree exponent in [2.1, 2.8] and 5-20% edge noise; every
+outer iteration contributes one (features, target) sample.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import api, synth
+
+NP = L.FA_GNN_NPARAMS
+FIN, HID = L.FA_GNN_FIN, L.FA_GNN_HIDDEN
+WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gnn_weights.json")
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters (He-scaled W1, small w2, zero biases),
+    rounded to values BF16 represents exactly."""
+    from .synth import bf16_representable
+    rng = synth.rng_for(seed)
+    th = np.zeros(NP, np.float32)
+    th[: FIN * HID] = rng.standard_normal(FIN * HID) * np.sqrt(2.0 / FIN)
+    th[FIN * HID + HID: FIN * HID + 2 * HID] = rng.standard_normal(HID) * np.sqrt(1.0 / HID)
+    return bf16_representable(th)
+
+
+class WarmStartModel:
+    """The device-resident model with its optimiser state and workspaces."""
+
+    def __init__(self, theta: np.ndarray | None = None, seed: int = 0, device="cuda"):
+        self.device = torch.device(device)
+        self.h = L.fa_gnn_create()
+        L.fa_gnn_set_params(self.h, init_params(seed) if theta is None else theta)
+        self.grad = torch.zeros(NP, dtype=torch.float32, device=self.device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self._ws = {}
+
+    def ws(self, n: int) -> torch.Tensor:
+        w = self._ws.get(n)
+        if w is None:
+            w = torch.empty(L.fa_gnn_workspace_floats(n), dtype=torch.float32, device=self.device)
+            self._ws[n] = w
+        return w
+
+    def features(self, graph: api.Graph, log_v1, corr_prev, F=None):
+        F = torch.empty((graph.n, FIN), dtype=torch.float32, device=self.device) if F is None else F
+        L.fa_gnn_features(graph.handle, log_v1, corr_prev, F, self.ws(graph.n))
+        return F
+
+    def predict(self, graph: api.Graph, F, out=None):
+        out = torch.empty(graph.n, dtype=torch.float32, device=self.device) if out is None else out
+        L.fa_gnn_forward(self.h, graph.handle, F, self.ws(graph.n), out)
+        return out
+
+    def train_step(self, graph: api.Graph, F, y, lr: float):
+        a = self.predict(graph, F)
+        L.fa_gnn_backward(self.h, graph.handle, self.ws(graph.n), a, y, self.grad, self.loss)
+        L.fa_gnn_adam_step(self.h, self.grad, lr)
+        return self.loss
+
+    def params(self) -> np.ndarray:
+        return L.fa_gnn_get_params(self.h)
+
+    def save(self, path: str = WEIGHTS_PATH, meta: dict | None = None):
+        with open(path, "w") as f:
+            json.dump({"nparams": NP, "theta": [float(x) for x in self.params()],
+                       "meta": meta or {}}, f, indent=0)
+
+    @staticmethod
+    def load(path: str = WEIGHTS_PATH, device="cuda") -> "WarmStartModel":
+        d = json.load(open(path))
+        return WarmStartModel(np.asarray(d["theta"], np.float32), device=device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.fa_gnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WarmStarter:
+    """Warm-start protocol for the solves of one alignment.
+
+    mode "cold":    no warm start (fa_sinkhorn's first b update uses v1).
+    mode "prev":    warm_log_v = log v1 + the previous solve's correction.
+    mode "learned": warm_log_v = log v1 + model(features).
+    Call ``before_solve`` right after fa_align_iter and ``after_solve``
+    after fa_sinkhorn."""
+
+    def __init__(self, aligner: api.Aligner, mode: str = "learned",
+                 model: WarmStartModel | None = None):
+        if mode == "learned" and model is None:
+            raise ValueError("learned warm start needs a model")
+        self.al, self.mode, self.model = aligner, mode, model
+        dev = aligner.device
+        n2 = aligner.n2
+        self.log_v1 = torch.empty(n2, dtype=torch.float32, device=dev)
+        self.corr = torch.zeros(n2, dtype=torch.float32, device=dev)
+        self.warm = torch.empty(n2, dtype=torch.float32, device=dev)
+        self.F = torch.empty((n2, FIN), dtype=torch.float32, device=dev)
+
+    def before_solve(self):
+        self.log_v1.copy_(self.al.log_v)
+        if self.mode == "cold":
+            return None
+        if self.mode == "prev":
+            L.fa_vec_axpby(self.al.n2, 1.0, self.log_v1, 1.0, self.corr, self.warm)
+            return self.warm
+        self.model.features(self.al.g2, self.log_v1, self.corr, self.F)
+        pred = self.model.predict(self.al.g2, self.F)
+        L.fa_vec_axpby(self.al.n2, 1.0, self.log_v1, 1.0, pred, self.warm)
+        return self.warm
+
+    def after_solve(self):
+        L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, -1.0, self.log_v1, self.corr)
+
+
+@dataclasses.dataclass
+class Sample:
+    graph: api.Graph          # column graph G2 (kept alive)
+    F: torch.Tensor           # n x 3 features
+    y: torch.Tensor           # n target corrections
+
+
+def training_pair(k: int, seed: int) -> synth.GraphPair:
+    """The k-th training pair: n ~ U[2000, 5000], exponent ~ U[2.1, 2.8],
+    edge noise ~ U[5%, 20%], 64-dim attributes, 5% anchors."""
+    rng = synth.rng_for(seed * 100003 + k)
+    n = int(rng.integers(2000, 5001))
+    gamma = float(rng.uniform(2.1, 2.8))
+    noise = float(rng.uniform(0.05, 0.20))
+    e1 = synth.chung_lu(n, gamma, 10.0, rng)
+    return synth.make_pair(e1, n, d=64, sigma=0.1, anchor_frac=0.05, frac_del=noise,
+                           frac_add=noise, rng=rng, name=f"train{k}", seed=seed)
+
+
+def generate_solves(n_pairs: int, outer: int, seed: int = 7, tol: float = 1e-5,
+                    max_sweeps: int = 20000, dtype: str = "f32", log=None):
+    """Run the method on training pairs and record, for every outer
+    iteration, the features and the converged correction of its solve."""
+    samples = []
+    model = WarmStartModel(seed=seed)            # only for its feature kernel
+    for k in range(n_pairs):
+        g = training_pair(k, seed)
+        G1, G2 = api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2)
+        al = api.Aligner(G1, G2, api.Params(dtype=dtype))
+        ws = WarmStarter(al, "cold")
+        al.node_cost(g.X1, g.X2, g.anchors)
+        al.plan_init()
+        for t in range(outer):
+            al.align_iter()
+            ws.before_solve()
+            F = model.features(G2, ws.log_v1, ws.corr)
+            al.sinkhorn(max_sweeps, tol, 10)
+            ws.after_solve()
+            samples.append(Sample(G2, F.clone(), ws.corr.clone()))
+        al.close()
+        if log and (k + 1) % 25 == 0:
+            log(f"generated {len(samples)} solves from {k + 1} pairs")
+    model.close()
+    return samples
+
+
+def train(samples, epochs: int = 20, lr: float = 3e-3, seed: int = 0, log=None):
+    model = WarmStartModel(seed=seed)
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        order = rng.permutation(len(samples))
+        losses = []
+        for i in order:
+            s = samples[i]
+            losses.append(model.train_step(s.graph, s.F, s.y, lr).clone())
+        ep_loss = float(torch.stack(losses).mean().item())
+        hist.append(ep_loss)
+        if log:
+            log(f"epoch {ep}: mean loss {ep_loss:.4e}")
+    return model, hist

@@ -270,3 +270,12 @@ def config_pair(name: str, n: int | None = None, seed: int | None = None,
                      anchor_frac=c["anchor_frac"], frac_del=c["frac_del"],
                      frac_add=c["frac_add"], rng=rng,
                      keep_nodes=c.get("keep"), name=name, seed=c["seed"])
+
+
+def bf16_representable(x: np.ndarray) -> np.ndarray:
+    """float32 values rounded (to nearest, ties to even) onto the bfloat16
+    grid, so that a BF16 copy of them is exact.  Used for seeded initial
+    weights that both sides of a parity test must see identically."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)

@@ -1,0 +1,79 @@
+"""The learned warm start's kernels (through the C ABI) against the FP64
+oracle: forward pass, gradient, one Adam step; and the gain of a trained
+model over the cold start."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fastalign_ref as R  # noqa: E402
+from oracle import gnn_ref as G  # noqa: E402
+from paper_2607_11952_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _case(n=700, seed=3):
+    from paper_2607_11952_gb300 import api, gnn
+    rng = synth.rng_for(seed)
+    e = synth.chung_lu(n, 2.3, 6.0, rng)
+    F = rng.standard_normal((n, G.FIN)).astype(np.float32)
+    y = rng.standard_normal(n).astype(np.float32)
+    theta = gnn.init_params(seed)
+    return api.Graph(n, e), e, F, y, theta
+
+
+def test_forward_and_gradient_match_oracle():
+    from paper_2607_11952_gb300 import gnn
+    graph, e, F, y, theta = _case()
+    n = graph.n
+    m = gnn.WarmStartModel(theta)
+    Fd, yd = torch.from_numpy(F).cuda(), torch.from_numpy(y).cuda()
+    a = m.predict(graph, Fd)
+    from paper_2607_11952_gb300 import _lib as L
+    L.fa_gnn_backward(m.h, graph.handle, m.ws(n), a, yd, m.grad, m.loss)
+    torch.cuda.synchronize()
+    A = R.row_normalized(n, e)
+    a_ref, _ = G.forward(A, F.astype(np.float64), theta.astype(np.float64))
+    loss_ref, g_ref = G.backward(A, F.astype(np.float64), theta.astype(np.float64), y)
+    np.testing.assert_allclose(a.cpu().numpy(), a_ref, rtol=1e-5, atol=1e-5)
+    assert abs(m.loss.item() - loss_ref) <= 1e-5 * loss_ref
+    g = m.grad.cpu().numpy().astype(np.float64)
+    scale = np.abs(g_ref[:-1]).max()
+    np.testing.assert_allclose(g[:-1], g_ref[:-1], rtol=0, atol=2e-5 * scale)
+    assert abs(g[-1]) < 1e-4
+
+
+def test_adam_step_matches_oracle():
+    from paper_2607_11952_gb300 import gnn
+    graph, e, F, y, theta = _case(seed=4)
+    m = gnn.WarmStartModel(theta)
+    Fd, yd = torch.from_numpy(F).cuda(), torch.from_numpy(y).cuda()
+    m.train_step(graph, Fd, yd, lr=1e-2)
+    torch.cuda.synchronize()
+    g = m.grad.cpu().numpy().astype(np.float64)
+    th_ref, _, _ = G.adam_step(theta.astype(np.float64), np.zeros(G.N_PARAMS), np.zeros(G.N_PARAMS),
+                               g, 1, lr=1e-2)
+    np.testing.assert_allclose(m.params(), th_ref, rtol=0, atol=1e-6)
+
+
+def test_training_reduces_loss():
+    from paper_2607_11952_gb300 import gnn
+    graph, e, F, y, theta = _case(seed=5)
+    # a target the model can represent: a smooth function of the features
+    A = R.row_normalized(graph.n, e)
+    y = (A @ np.tanh(F[:, 0] + 0.5 * F[:, 2])).astype(np.float32)
+    m = gnn.WarmStartModel(theta)
+    Fd, yd = torch.from_numpy(F).cuda(), torch.from_numpy(y).cuda()
+    first = m.train_step(graph, Fd, yd, lr=5e-3).item()
+    for _ in range(300):
+        last = m.train_step(graph, Fd, yd, lr=5e-3)
+    assert last.item() < 0.5 * first
