@@ -256,6 +256,12 @@ fa_status fa_gnn_backward(fa_gnn* m, const fa_graph* g, const float* ws,
 fa_status fa_gnn_adam_step(fa_gnn* m, const float* grad, float lr,
                            float beta1, float beta2, float eps,
                            fa_stream_t stream);
+/* The warm start handed to fa_sinkhorn: out = log_v1 + clamp(pred,
+ * -max_abs, max_abs) (device vectors of n floats); a non-finite prediction
+ * leaves that column at its cold value.  Bounding the correction keeps the
+ * FP32 column scaling finite whatever the model predicts. */
+fa_status fa_gnn_warm_start(int32_t n, const float* log_v1, const float* pred,
+                            float max_abs, float* out, fa_stream_t stream);
 /* out = a x + b y on device vectors of n floats (y nullable = 0). */
 fa_status fa_vec_axpby(int32_t n, float a, const float* x, float b,
                        const float* y, float* out, fa_stream_t stream);

@@ -88,6 +88,7 @@ SIGNATURES = {
     "fa_gnn_adam_step": (_i32, [_p, _p, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_float, _p]),
     "fa_vec_axpby": (_i32, [_i32, ctypes.c_float, _p, ctypes.c_float, _p, _p, _p]),
+    "fa_gnn_warm_start": (_i32, [_i32, _p, _p, ctypes.c_float, _p, _p]),
 }
 FA_GNN_FIN, FA_GNN_HIDDEN = 3, 64
 FA_GNN_NPARAMS = FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1
@@ -299,3 +300,8 @@ def fa_gnn_adam_step(m, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None)
 def fa_vec_axpby(n, a, x, b, y, out, stream=None) -> None:
     _check(lib().fa_vec_axpby(int(n), float(a), ptr(x), float(b), ptr(y), ptr(out),
                               stream_ptr(stream)), "fa_vec_axpby")
+
+
+def fa_gnn_warm_start(n, log_v1, pred, max_abs, out, stream=None) -> None:
+    _check(lib().fa_gnn_warm_start(int(n), ptr(log_v1), ptr(pred), float(max_abs), ptr(out),
+                                   stream_ptr(stream)), "fa_gnn_warm_start")

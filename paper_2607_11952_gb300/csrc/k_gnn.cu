@@ -247,6 +247,17 @@ __global__ void k_gnn_sync_bf16(const float* __restrict__ theta, __nv_bfloat16* 
   else if (p >= kOffW2 && p < kOffC) w2[p - kOffW2] = __float2bfloat16_rn(theta[p]);
 }
 
+// warm start: out = log_v1 + clamp(pred, -max_abs, max_abs); a non-finite
+// prediction contributes 0 (the cold start for that column)
+__global__ void k_gnn_warm(int n, const float* __restrict__ lv1, const float* __restrict__ pred,
+                           float max_abs, float* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float p = pred[i];
+  p = isfinite(p) ? fminf(fmaxf(p, -max_abs), max_abs) : 0.f;
+  out[i] = lv1[i] + p;
+}
+
 __global__ void k_axpby(int n, float a, const float* __restrict__ x, float b,
                         const float* __restrict__ y, float* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -386,6 +397,18 @@ fa_status fa_gnn_adam_step(fa_gnn* g, const float* grad, float lr, float beta1, 
   k_gnn_adam<<<(kNP + 255) / 256, 256, 0, s>>>(g->theta, g->m, g->v, grad, lr, beta1, beta2, eps,
                                                (int)g->step, g->W1, g->w2);
   FA_LAUNCHED("k_gnn_adam");
+  return FA_OK;
+}
+
+fa_status fa_gnn_warm_start(int32_t n, const float* log_v1, const float* pred, float max_abs,
+                            float* out, fa_stream_t stream) {
+  if (n < 1 || !log_v1 || !pred || !out || !(max_abs > 0.f)) {
+    set_error("fa_gnn_warm_start: bad argument");
+    return FA_ERR_ARG;
+  }
+  k_gnn_warm<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(n, log_v1, pred,
+                                                                                 max_abs, out);
+  FA_LAUNCHED("k_gnn_warm");
   return FA_OK;
 }
 

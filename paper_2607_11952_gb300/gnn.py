@@ -107,7 +107,9 @@ class WarmStarter:
     mode "prev":    warm_log_v = log v1 + the previous solve's correction.
     mode "learned": warm_log_v = log v1 + model(features).
     Call ``before_solve`` right after fa_align_iter and ``after_solve``
-    after fa_sinkhorn."""
+    after fa_sinkhorn, or ``solve`` for both with the cold-start fallback."""
+
+    MAX_CORR = 20.0     # bound on a predicted correction (natural-log units)
 
     def __init__(self, aligner: api.Aligner, mode: str = "learned",
                  model: WarmStartModel | None = None):
@@ -130,11 +132,28 @@ class WarmStarter:
             return self.warm
         self.model.features(self.al.g2, self.log_v1, self.corr, self.F)
         pred = self.model.predict(self.al.g2, self.F)
-        L.fa_vec_axpby(self.al.n2, 1.0, self.log_v1, 1.0, pred, self.warm)
+        L.fa_gnn_warm_start(self.al.n2, self.log_v1, pred, self.MAX_CORR, self.warm)
         return self.warm
 
     def after_solve(self):
         L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, -1.0, self.log_v1, self.corr)
+
+    def solve(self, max_iter: int, tol: float, check_every: int = 5):
+        """One warm-started solve; if it meets NaN/Inf (a bad prediction),
+        the cold start runs from the same kernel instead.  Returns
+        (iterations, error, status, used_fallback)."""
+        warm = self.before_solve()
+        try:
+            it, err, st = self.al.sinkhorn(max_iter, tol, check_every, warm)
+            fell_back = False
+        except L.FastAlignError as e:
+            if warm is None or e.status != L.FA_ERR_NUMERIC:
+                raise
+            self.al.log_v.copy_(self.log_v1)
+            it, err, st = self.al.sinkhorn(max_iter, tol, check_every, None)
+            fell_back = True
+        self.after_solve()
+        return it, err, st, fell_back
 
 
 @dataclasses.dataclass

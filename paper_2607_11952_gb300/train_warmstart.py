@@ -51,10 +51,18 @@ def evaluate(g: synth.GraphPair, model: gnn.WarmStartModel, outer: int = 6,
             al.log_v.copy_(v0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            it, err, st = al.sinkhorn(max_sweeps, tol, check_every, warm)
+            fell_back = False
+            try:
+                it, err, st = al.sinkhorn(max_sweeps, tol, check_every, warm)
+            except L.FastAlignError as e:        # cold-start fallback
+                if e.status != L.FA_ERR_NUMERIC:
+                    raise
+                al.log_v.copy_(v0)
+                it, err, st = al.sinkhorn(max_sweeps, tol, check_every, None)
+                fell_back = True
             torch.cuda.synchronize()
             res[mode] = {"iters": int(it), "ms": (time.perf_counter() - t0) * 1e3,
-                         "err": float(err), "status": int(st)}
+                         "err": float(err), "status": int(st), "fallback": fell_back}
         ws.after_solve()          # the trajectory continues from the learned solve
         rows.append(res)
     hits = al.hits_mrr(g.test_pairs)
@@ -73,20 +81,27 @@ def main(argv=None):
     ap.add_argument("--eval-outer", type=int, default=6)
     ap.add_argument("--out", default=gnn.WEIGHTS_PATH)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--eval-only", action="store_true",
+                    help="evaluate the weights in --out without training")
     args = ap.parse_args(argv)
 
     def log(s):
         print(s, flush=True)
 
-    t0 = time.time()
-    samples = gnn.generate_solves(args.pairs, args.outer, seed=args.seed, log=log)
-    t1 = time.time()
-    log(f"{len(samples)} solves generated in {t1 - t0:.1f} s")
-    model, hist = gnn.train(samples, epochs=args.epochs, lr=args.lr, seed=args.seed, log=log)
-    t2 = time.time()
-    log(f"trained in {t2 - t1:.1f} s")
-    model.save(args.out, meta={"pairs": args.pairs, "outer": args.outer, "epochs": args.epochs,
-                               "lr": args.lr, "seed": args.seed, "loss": hist})
+    t0 = t1 = t2 = time.time()
+    samples, hist = [], []
+    if args.eval_only:
+        model = gnn.WarmStartModel.load(args.out)
+    else:
+        samples = gnn.generate_solves(args.pairs, args.outer, seed=args.seed, log=log)
+        t1 = time.time()
+        log(f"{len(samples)} solves generated in {t1 - t0:.1f} s")
+        model, hist = gnn.train(samples, epochs=args.epochs, lr=args.lr, seed=args.seed, log=log)
+        t2 = time.time()
+        log(f"trained in {t2 - t1:.1f} s")
+        model.save(args.out, meta={"pairs": args.pairs, "outer": args.outer,
+                                   "epochs": args.epochs, "lr": args.lr, "seed": args.seed,
+                                   "loss": hist})
     g = synth.config_pair("cl20k", n=args.eval_n)
     rows, hits = evaluate(g, model, outer=args.eval_outer)
     tot = {m: {"iters": sum(r[m]["iters"] for r in rows), "ms": sum(r[m]["ms"] for r in rows)}
