@@ -236,7 +236,8 @@ fa_status fa_gnn_get_params(const fa_gnn* g, float* host_theta);
 int64_t fa_gnn_workspace_floats(int32_t n);
 
 /* Per-node inputs F (device, n x 3 row-major) of the column graph g2:
- * (log_v1_j - mean log_v1, corr_prev_j, log(1 + deg_j)); corr_prev
+ * (log_v1_j - mean log_v1, corr_prev_j - mean corr_prev, log(1 + deg_j))
+ * (potentials are defined up to a constant, so both are centred); corr_prev
  * (device, n, nullable = zeros) is the previous solve's correction.
  * ws: workspace of fa_gnn_workspace_floats(n). */
 fa_status fa_gnn_features(const fa_graph* g2, const float* log_v1,

@@ -89,8 +89,9 @@ def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def features(Abar_deg: np.ndarray, log_v1: np.ndarray, corr_prev: np.ndarray) -> np.ndarray:
-    """Per-node inputs: centred cold first column update, the previous
-    solve's correction, log(1 + degree)."""
+    """Per-node inputs: centred cold first column update, centred previous
+    correction (potentials are defined up to a constant), log(1 + degree)."""
     lv = np.asarray(log_v1, np.float64)
-    return np.stack([lv - lv.mean(), np.asarray(corr_prev, np.float64),
+    cp = np.asarray(corr_prev, np.float64)
+    return np.stack([lv - lv.mean(), cp - cp.mean(),
                      np.log1p(np.asarray(Abar_deg, np.float64))], axis=1)

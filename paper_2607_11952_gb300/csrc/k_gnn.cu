@@ -75,14 +75,15 @@ __global__ void __launch_bounds__(1024) k_means(int n, const float* __restrict__
 }
 
 // ------------------------------------------------------------ features
-// F[j] = (log_v1_j - mean log_v1, corr_prev_j, log(1 + deg_j))
+// F[j] = (log_v1_j - mean log_v1, corr_prev_j - mean corr_prev, log(1 + deg_j));
+// both potentials are centred: they are defined up to a constant
 __global__ void k_gnn_features(int n, const int32_t* __restrict__ rp, const float* __restrict__ lv,
                                const float* __restrict__ corr, const float* __restrict__ mean,
                                float* __restrict__ F) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   F[(size_t)j * kFin + 0] = lv[j] - mean[0];
-  F[(size_t)j * kFin + 1] = corr ? corr[j] : 0.f;
+  F[(size_t)j * kFin + 1] = corr ? corr[j] - mean[1] : 0.f;
   F[(size_t)j * kFin + 2] = log1pf((float)(rp[j + 1] - rp[j]));
 }
 
@@ -341,7 +342,7 @@ fa_status fa_gnn_features(const fa_graph* g2, const float* log_v1, const float* 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int n = g2->d.n;
   GnnWs w = ws_layout(ws, n);
-  k_means<<<1, 1024, 0, s>>>(n, log_v1, nullptr, w.scal);
+  k_means<<<1, 1024, 0, s>>>(n, log_v1, corr_prev, w.scal);
   FA_LAUNCHED("k_means");
   k_gnn_features<<<(n + 255) / 256, 256, 0, s>>>(n, g2->d.row_ptr, log_v1, corr_prev, w.scal, F);
   FA_LAUNCHED("k_gnn_features");

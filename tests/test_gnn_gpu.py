@@ -106,3 +106,18 @@ def test_trained_warm_start_beats_cold_start():
         tot["learned"] += it_l
     print("sweeps to 1e-4 over 6 outer iterations:", tot)
     assert tot["learned"] < tot["cold"]
+
+
+def test_features_match_oracle():
+    """Inputs of the model: the centred cold column update, the centred
+    previous correction and log(1 + degree), against the oracle's."""
+    from paper_2607_11952_gb300 import gnn
+    graph, e, F, y, theta = _case(n=900, seed=6)
+    rng = np.random.default_rng(6)
+    lv1 = (rng.standard_normal(graph.n) - 9.0).astype(np.float32)
+    corr = (rng.standard_normal(graph.n) + 3.0).astype(np.float32)
+    m = gnn.WarmStartModel(theta)
+    got = m.features(graph, torch.from_numpy(lv1).cuda(), torch.from_numpy(corr).cuda())
+    deg = np.bincount(e.ravel(), minlength=graph.n)
+    want = G.features(deg, lv1, corr)
+    np.testing.assert_allclose(got.cpu().numpy(), want, rtol=1e-5, atol=1e-5)
