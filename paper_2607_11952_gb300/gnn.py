@@ -124,7 +124,7 @@ class WarmStarter:
         self.F = torch.empty((n2, FIN), dtype=torch.float32, device=dev)
 
     def before_solve(self):
-        self.log_v1.copy_(self.al.log_v)
+        L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, 0.0, None, self.log_v1)
         if self.mode == "cold":
             return None
         if self.mode == "prev":
@@ -149,7 +149,7 @@ class WarmStarter:
         except L.FastAlignError as e:
             if warm is None or e.status != L.FA_ERR_NUMERIC:
                 raise
-            self.al.log_v.copy_(self.log_v1)
+            L.fa_vec_axpby(self.al.n2, 1.0, self.log_v1, 0.0, None, self.al.log_v)
             it, err, st = self.al.sinkhorn(max_iter, tol, check_every, None)
             fell_back = True
         self.after_solve()
