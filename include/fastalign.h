@@ -267,6 +267,39 @@ fa_status fa_gnn_warm_start(int32_t n, const float* log_v1, const float* pred,
 fa_status fa_vec_axpby(int32_t n, float a, const float* x, float b,
                        const float* y, float* out, fa_stream_t stream);
 
+/* ----------------------------------------------------------------------
+ * fa_sinkhorn_step_static -- one fused Sinkhorn iteration that allocates
+ * no device memory.  The paper has no counterpart: this entry serves
+ * callers that cannot allocate device memory while they run, for example a
+ * serving process whose memory budget is fixed at start-up (another
+ * framework owns the device memory pool and forbids raw allocations), or a
+ * latency-critical loop that cannot afford cudaMalloc's cost and implicit
+ * synchronisation.  It needs no fa_ctx (creating one allocates).
+ *
+ * Computes, exactly as one iteration of fa_sinkhorn: u_i = mu_i /
+ * sum_j K_ij v_j (log_u, n1), the next column scaling from the column sums
+ * sum_i K_ij u_i (log_v_next, n2) and the L1 column-marginal error of the
+ * plan (log_u, log_v) into *err (device double), with mu = 1/n1 and
+ * nu = 1/n2.  K: device, n1 x ld, FA_F32 or FA_BF16 (dtype), 16-byte
+ * aligned, padding columns 0; log_v, log_u, log_v_next, err: device.
+ * status (device int32, nullable) receives the kernels' status bits
+ * (1: NaN/Inf or an all-zero row or column, 2: a bounded wait gave up).
+ *
+ * Scratch: file-scope static device arrays reserved when the library is
+ * loaded (8 MiB of partial column sums plus small counters) and held by
+ * every GPU that loads the library until the process exits.  Limit: ld <=
+ * 65536 columns (FA_ERR_UNSUPPORTED beyond); ld must be a multiple of 128.
+ * The first call on a device looks the arrays' device addresses up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the same scratch: calls that can overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Asynchronous on `stream`.
+ * -------------------------------------------------------------------- */
+fa_status fa_sinkhorn_step_static(const void* K, int32_t dtype, int32_t n1,
+                                  int32_t n2, int64_t ld, const float* log_v,
+                                  float* log_u, float* log_v_next, double* err,
+                                  int32_t* status, fa_stream_t stream);
+
 /* Per-thread description of the last error. */
 const char* fa_last_error_string(void);
 

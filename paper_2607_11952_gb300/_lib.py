@@ -89,6 +89,7 @@ SIGNATURES = {
                                 ctypes.c_float, _p]),
     "fa_vec_axpby": (_i32, [_i32, ctypes.c_float, _p, ctypes.c_float, _p, _p, _p]),
     "fa_gnn_warm_start": (_i32, [_i32, _p, _p, ctypes.c_float, _p, _p]),
+    "fa_sinkhorn_step_static": (_i32, [_p, _i32, _i32, _i32, _i64, _p, _p, _p, _p, _p, _p]),
 }
 FA_GNN_FIN, FA_GNN_HIDDEN = 3, 64
 FA_GNN_NPARAMS = FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1
@@ -305,3 +306,11 @@ def fa_vec_axpby(n, a, x, b, y, out, stream=None) -> None:
 def fa_gnn_warm_start(n, log_v1, pred, max_abs, out, stream=None) -> None:
     _check(lib().fa_gnn_warm_start(int(n), ptr(log_v1), ptr(pred), float(max_abs), ptr(out),
                                    stream_ptr(stream)), "fa_gnn_warm_start")
+
+
+def fa_sinkhorn_step_static(K, dtype, n1, n2, ld, log_v, log_u, log_v_next, err, status=None,
+                            stream=None) -> None:
+    _check(lib().fa_sinkhorn_step_static(ptr(K), int(dtype), int(n1), int(n2), int(ld),
+                                         ptr(log_v), ptr(log_u), ptr(log_v_next), ptr(err),
+                                         ptr(status), stream_ptr(stream)),
+           "fa_sinkhorn_step_static")
