@@ -196,7 +196,7 @@ def run_ours(args):
         al32.close()
 
     # end to end through the public API from host buffers
-    e2e = _e2e(args, g, dev, api, step_fn=None) if args.e2e else None
+    e2e = _e2e(args, g, dev, api, model) if args.e2e else None
 
     cpu = (_cpu_baseline(args, total_sweeps / args.steps)
            if (rank == 0 and world == 1 and args.cpu_baseline) else None)
@@ -246,10 +246,12 @@ def _ncu_traffic(args):
     return e.get("dram_bytes_per_launch_full_size") if e else None
 
 
-def _e2e(args, g, dev, api, step_fn=None):
+def _e2e(args, g, dev, api, model):
     """Same step through the public API from host buffers: graph build
     (host CSR + upload), attribute upload from pinned memory, the whole
-    alignment and the read-back of the top-10 indices."""
+    alignment with the same warm start and the read-back of the top-10
+    indices."""
+    from paper_2607_11952_gb300 import gnn
     import numpy as np
     import torch
     X1h = torch.from_numpy(g.X1).pin_memory()
@@ -265,9 +267,10 @@ def _e2e(args, g, dev, api, step_fn=None):
         X2 = X2h.to(dev, non_blocking=True)
         al.node_cost(X1, X2, g.anchors)
         al.plan_init()
+        ws = gnn.WarmStarter(al, args.warm, model if args.warm == "learned" else None)
         for _ in range(args.outer):
             al.align_iter()
-            al.sinkhorn(args.max_sweeps, args.tol, args.check_every)
+            ws.solve(args.max_sweeps, args.tol, args.check_every)
         idx, score = al.topk(10)
         out = idx.cpu().numpy()
         torch.cuda.synchronize()

@@ -28,155 +28,11 @@
 #include <stdlib.h>
 
 #include "fa_internal.cuh"
+#include "sweep_dev.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace fa {
-
-// ------------------------------------------------------------ K element types
-template <typename TK> struct KT;
-template <> struct KT<float> {
-  static constexpr int V = 4;
-  __device__ static __forceinline__ void unpack(const uint4& u, float (&f)[4]) {
-    f[0] = __uint_as_float(u.x); f[1] = __uint_as_float(u.y);
-    f[2] = __uint_as_float(u.z); f[3] = __uint_as_float(u.w);
-  }
-};
-template <> struct KT<__nv_bfloat16> {
-  static constexpr int V = 8;
-  // bf16 is the upper half of an fp32: widen by shifting, register-only.
-  __device__ static __forceinline__ void unpack(const uint4& u, float (&f)[8]) {
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      f[2 * q] = __uint_as_float(w[q] << 16);
-      f[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
-    }
-  }
-};
-
-// Packed pairs of fp32 in one 64-bit register pair, for the paired FMA of
-// sm_100+ (fma.rn.f32x2): one instruction per two elements.
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t pk2(float lo, float hi) {
-  f2_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ f2_t pk2u(uint32_t lo, uint32_t hi) {
-  f2_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 upk2(f2_t v) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-  return r;
-}
-__device__ __forceinline__ f2_t ffma2(f2_t a, f2_t b, f2_t c) {
-  f2_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-// the 16 bytes of K as V/2 packed fp32 pairs (columns 2k, 2k+1)
-__device__ __forceinline__ void pairs(const uint4& u, f2_t (&p)[2], float) {
-  p[0] = pk2u(u.x, u.y);
-  p[1] = pk2u(u.z, u.w);
-}
-__device__ __forceinline__ void pairs(const uint4& u, f2_t (&p)[4], __nv_bfloat16) {
-  // bf16 is the upper half of an fp32: widen by shift / mask
-  p[0] = pk2u(u.x << 16, u.x & 0xffff0000u);
-  p[1] = pk2u(u.y << 16, u.y & 0xffff0000u);
-  p[2] = pk2u(u.z << 16, u.z & 0xffff0000u);
-  p[3] = pk2u(u.w << 16, u.w & 0xffff0000u);
-}
-
-// One 16-byte shared-memory load (a single LDS.128 per thread).
-__device__ __forceinline__ uint4 lds128(const void* p) {
-  uint4 r;
-  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-               : "r"((uint32_t)__cvta_generic_to_shared(p)));
-  return r;
-}
-
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait on an mbarrier phase: false after about 2 s (the caller then
-// records ST_TIMEOUT and stops depending on that data).
-constexpr uint64_t kWaitNs = 2000000000ull;
-__device__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
-  if (mbar_try(a, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < (1u << 28); ++it) {
-    if (mbar_try(a, parity)) return true;
-    if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_size() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %cluster_nctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t map_cluster(uint32_t local_smem_addr, uint32_t cta) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_smem_addr), "r"(cta));
-  return r;
-}
-// 4-byte store into a peer CTA's shared memory that completes as 4
-// transaction bytes on the peer's mbarrier (no fence needed on either side).
-__device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint32_t remote_mbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
-                   remote_addr),
-               "r"(__float_as_uint(v)), "r"(remote_mbar)
-               : "memory");
-}
 
 // ------------------------------------------------------------ plan init
 // T0 = mu nu^T (reading: independent coupling): K = 1, log u = log mu,
@@ -287,8 +143,14 @@ constexpr size_t kSmemBudget = 220 * 1024;
 // and re-armed it, so kNX = 4 slots never alias.  One cluster barrier after
 // the mbarrier initialisation and one before exit bracket all remote
 // traffic; every mbarrier wait is bounded.
+// CTAs per SM a launch shape is built for: 256-thread CTAs whose threads own
+// at most 16 elements of a row run four to an SM, wider ones two.
+__host__ __device__ constexpr int sweep_ctas_per_sm(int NT, int elems_per_thread) {
+  return NT == 256 ? (elems_per_thread <= 16 ? 4 : 2) : 1;
+}
+
 template <typename TK, int S, int R, int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k_sweep(
+__global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sweep(
     const TK* __restrict__ K, int64_t ld, int n1, int n2, int W, int NS,
     const float* __restrict__ log_v, float* __restrict__ log_u, float mu,
     float log_mu, float* __restrict__ colpart, int* __restrict__ status) {
@@ -537,6 +399,12 @@ static int env_int(const char* name, int dflt) {
   return atoi(v);
 }
 
+// warp-specialised sweep (k_sweep_ws.cu)
+void* sweep_ws_kernel(bool bf16, int S, int R);
+size_t sweep_ws_smem(int NS, int R, int W, bool bf16);
+int sweep_ws_threads();
+int sweep_ws_compute_threads();
+
 static size_t sweep_smem(const SweepPlan& sp, bool bf16) {
   const size_t b = bf16 ? 2 : 4;
   return (size_t)sp.NS * sp.R * sp.W * b + (size_t)(kMaxNS + kNX) * 8 +
@@ -546,9 +414,75 @@ static size_t sweep_smem(const SweepPlan& sp, bool bf16) {
 // Pick the smallest cluster whose column slab fits the register budget and
 // leaves at least 3 ring stages (2 for very wide rows); R = 2 rows per step
 // when the ring still has >= 3 stages.  FA_SWEEP_{Q,R,NS} override (tuning).
+// Warp-specialised sweep (k_sweep_ws.cu): 8 compute warps (256 threads own
+// the slab), two CTAs per SM; smallest cluster whose slab fits the
+// instantiated register shapes, R up to 4 (BF16) or 2 rows per step with
+// Q R <= 32, and a ring of at least L + 2 stages (L + 1 for very wide rows).
+static SweepPlan plan_sweep_ws(int64_t ld, bool bf16) {
+  SweepPlan sp;
+  sp.Q = 0;
+  sp.kind = 1;
+  const int V = bf16 ? 8 : 4;
+  const size_t b = bf16 ? 2 : 4;
+  int L = env_int("FA_SWEEP_L", 1);
+  L = L < 1 ? 1 : (L > 2 ? 2 : L);
+  const int Qforce = env_int("FA_SWEEP_Q", 0);
+  const int Rforce = env_int("FA_SWEEP_R", 0);
+  const int NSforce = env_int("FA_SWEEP_NS", 0);
+  const int NTC = sweep_ws_compute_threads();
+  const int smax = bf16 ? 4 : 8;   // register shapes that run without spills
+  const size_t budget = kSmemBudget / 2;
+  for (int pass = 0; pass < 2 && sp.Q == 0; ++pass) {
+    const int min_ns = pass == 0 ? L + 2 : L + 1;
+    for (int Q = 1; Q <= kMaxQ && sp.Q == 0; Q *= 2) {
+      if (Qforce && Q != Qforce) continue;
+      if (ld % Q) continue;
+      const int64_t W = ld / Q;
+      if ((W * (int64_t)b) % 16) continue;
+      const int S = (int)((W + (int64_t)NTC * V - 1) / ((int64_t)NTC * V));
+      if (S > smax) continue;
+      for (int R = bf16 ? 4 : 2; R >= 1; R /= 2) {
+        if (Rforce && R != Rforce) continue;
+        if (Q * R > 32) continue;
+        const size_t fixed = sweep_ws_smem(0, R, (int)W, bf16);
+        int NS = (int)((budget - fixed) / ((size_t)R * W * b));
+        if (NS > kMaxNS) NS = kMaxNS;
+        if (NSforce) NS = NSforce < NS ? NSforce : NS;
+        if (NS >= min_ns) {
+          sp.Q = Q;
+          sp.W = (int)W;
+          sp.S = S;
+          sp.R = R;
+          sp.NS = NS;
+          sp.NT = NTC;
+          sp.L = L;
+          break;
+        }
+      }
+    }
+  }
+  return sp;
+}
+
 SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   SweepPlan sp;
   sp.Q = 0;
+  if (env_int("FA_SWEEP_KIND", 0) != 0) {
+    sp = plan_sweep_ws(ld, bf16);
+    if (sp.Q > 0) {
+      int G = env_int("FA_SWEEP_G", 0);
+      if (G <= 0) G = max_G;
+      const int steps = (n1 + sp.R - 1) / sp.R;
+      if (G > steps) G = steps;
+      if (G > max_G) G = max_G;
+      if (G < 1) G = 1;
+      sp.G = G;
+      return sp;
+    }
+    sp = SweepPlan();   // no warp-specialised shape: fall back below
+    sp.Q = 0;
+  }
+  sp.kind = 0;
   const int V = bf16 ? 8 : 4;
   const size_t b = bf16 ? 2 : 4;
   const int Qforce = env_int("FA_SWEEP_Q", 0);
@@ -560,8 +494,9 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   // CTAs per SM is as fast or faster than 512 (one CTA) and 1024 threads
   const int nt_env = env_int("FA_SWEEP_NT", 256);
   const int NT = (nt_env == 256 || nt_env == 1024) ? nt_env : 512;
-  const int smax = NT == 1024 ? (bf16 ? 3 : 6) : (bf16 ? kSmaxBF16 : kSmaxF32);
-  const size_t budget = NT == 256 ? kSmemBudget / 2 : kSmemBudget;
+  int smax = NT == 1024 ? (bf16 ? 3 : 6) : (bf16 ? kSmaxBF16 : kSmaxF32);
+  const int smax_env = env_int("FA_SWEEP_SMAX", 0);
+  if (smax_env > 0 && smax_env < smax) smax = smax_env;
   for (int pass = 0; pass < 2 && sp.Q == 0; ++pass) {
     const int min_ns = pass == 0 ? 3 : 2;
     for (int Q = 1; Q <= kMaxQ && sp.Q == 0; Q *= 2) {
@@ -571,6 +506,7 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
       if ((W * (int64_t)b) % 16) continue;
       const int S = (int)((W + (int64_t)NT * V - 1) / ((int64_t)NT * V));
       if (S > smax) continue;
+      const size_t budget = kSmemBudget / sweep_ctas_per_sm(NT, S * V);
       for (int R = bf16 ? 4 : 2; R >= 1; R /= 2) {
         if (Rforce && R != Rforce) continue;
         const size_t fixed = (size_t)(kMaxNS + kNX) * 8 + (size_t)(2 * R * (NT / 32) + kNX * kMaxQ * R) * 4;
@@ -600,12 +536,19 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   return sp;
 }
 
+static size_t sweep_dyn_smem(const SweepPlan& sp, bool bf16) {
+  return sp.kind ? sweep_ws_smem(sp.NS, sp.R, sp.W, bf16) : sweep_smem(sp, bf16);
+}
+static void* sweep_fn(const SweepPlan& sp, bool bf16) {
+  return sp.kind ? sweep_ws_kernel(bf16, sp.S, sp.R) : sweep_kernel(bf16, sp.S, sp.R, sp.NT);
+}
+
 static cudaLaunchConfig_t sweep_config(const SweepPlan& sp, bool bf16, unsigned grid,
                                        cudaLaunchAttribute* attr, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3((unsigned)sp.NT);
-  cfg.dynamicSmemBytes = sweep_smem(sp, bf16);
+  cfg.blockDim = dim3((unsigned)(sp.kind ? sweep_ws_threads() : sp.NT));
+  cfg.dynamicSmemBytes = sweep_dyn_smem(sp, bf16);
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)sp.Q;
@@ -618,7 +561,7 @@ static cudaLaunchConfig_t sweep_config(const SweepPlan& sp, bool bf16, unsigned 
 
 static cudaError_t prepare_sweep(void* fn, const SweepPlan& sp, bool bf16) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sweep_smem(sp, bf16));
+                                       (int)sweep_dyn_smem(sp, bf16));
   if (e != cudaSuccess) return e;
   if (sp.Q > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
@@ -632,7 +575,7 @@ fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
     set_error("fa_sinkhorn: no cluster shape fits a row of %lld elements", (long long)ld);
     return FA_ERR_UNSUPPORTED;
   }
-  void* fn = sweep_kernel(bf16, sp.S, sp.R, sp.NT);
+  void* fn = sweep_fn(sp, bf16);
   if (!fn) {
     set_error("fa_sinkhorn: no sweep kernel for S=%d R=%d", sp.S, sp.R);
     return FA_ERR_UNSUPPORTED;
@@ -645,23 +588,26 @@ fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = sweep_config(sp, bf16, (unsigned)(sp.G * sp.Q), attr, s);
   const float log_mu = logf(mu);
-  int W = sp.W, NS = sp.NS;
+  int W = sp.W, NS = sp.NS, L = sp.L;
   void* args[] = {(void*)&K, (void*)&ld, (void*)&n1, (void*)&n2, (void*)&W,
                   (void*)&NS, (void*)&log_v, (void*)&log_u, (void*)&mu,
                   (void*)&log_mu, (void*)&colpart, (void*)&status};
-  e = cudaLaunchKernelExC(&cfg, fn, args);
+  void* args_ws[] = {(void*)&K, (void*)&ld, (void*)&n1, (void*)&n2, (void*)&W,
+                     (void*)&NS, (void*)&L, (void*)&log_v, (void*)&log_u, (void*)&mu,
+                     (void*)&log_mu, (void*)&colpart, (void*)&status};
+  e = cudaLaunchKernelExC(&cfg, fn, sp.kind ? args_ws : args);
   if (e != cudaSuccess) {
     set_error("k_sweep launch (Q=%d S=%d R=%d NS=%d G=%d): %s", sp.Q, sp.S, sp.R,
               sp.NS, sp.G, cudaGetErrorString(e));
     return FA_ERR_CUDA;
   }
-  FA_LAUNCHED("k_sweep");
+  if (sp.kind) FA_LAUNCHED("k_sweep_ws"); else FA_LAUNCHED("k_sweep");
   return FA_OK;
 }
 
 // Number of clusters of the chosen shape that fit on the device at once.
 int sweep_max_active_clusters(const SweepPlan& sp, bool bf16) {
-  void* fn = sweep_kernel(bf16, sp.S, sp.R, sp.NT);
+  void* fn = sweep_fn(sp, bf16);
   if (!fn || sp.Q < 1) return 0;
   if (prepare_sweep(fn, sp, bf16) != cudaSuccess) {
     cudaGetLastError();

@@ -14,6 +14,8 @@
 // GPU form of the paper's column-blocked SpMM, Section 3.4).
 #include <math.h>
 
+#include <stdlib.h>
+
 #include "fa_internal.cuh"
 
 namespace fa {
@@ -166,22 +168,38 @@ fa_status launch_normalize_rows(int n, int d, const float* X, int64_t ldx,
 
 // ------------------------------------------------------------ left SpMM
 // W^T[j, i] = sum_k P[i,k] s_k D[k, j]  for NV value sets P in {va, vb}.
-// CTA tile: 32 rows i x 64 columns j.  Warp w computes rows 4w..4w+3, lane l
-// columns 2l, 2l+1 (one 128/256-byte coalesced gather per neighbour row),
-// then the tile is transposed through shared memory and stored as 32
-// consecutive i per column j (NV floats per element).  blockIdx.x runs over
-// row tiles first, so all row tiles of one 64-column panel of D run
-// back-to-back and the panel (n1 x 64 elements) stays in L2.
-template <int NV> struct VecF;
-template <> struct VecF<1> { using T = float; };
-template <> struct VecF<2> { using T = float2; };
+// CTA tile: 32 rows i x 128 columns j.  The tile's neighbour lists are one
+// contiguous CSR range [rp[i0], rp[i0+32]), split evenly over the 8 warps by
+// edge count, so high-degree rows are shared and warps finish together.  A
+// warp loads 32 edges at a time lane-parallel (neighbour k, weights times
+// s_k, output row by binary search in the tile's row pointers), broadcasts
+// them and keeps kGU row gathers of D[k, j0:j0+128] in flight (lane l:
+// columns 4l..4l+3, 256 B per gather in BF16, 512 B in FP32).  A finished row
+// goes to a shared-memory tile (atomics only for a row shared with another
+// warp); the tile is then stored transposed, 32 consecutive i per column j
+// (NV floats per element).  blockIdx.x runs over row tiles first, so all row
+// tiles of one 128-column panel of D run back-to-back and the panel
+// (n1 x 128 elements) stays in L2.
+constexpr int kGU = 8;     // gathers in flight per warp
 
-__device__ __forceinline__ float2 load_pair(const float* p) {
-  return __ldg(reinterpret_cast<const float2*>(p));
+// Largest t in [0, n) with p[t] <= e, for p[0] <= e < p[n] (p nondecreasing).
+template <int N>
+__device__ __forceinline__ int seg_of(const int* p, int e) {
+  int lo = 0, hi = N;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
 }
-__device__ __forceinline__ float2 load_pair(const __nv_bfloat16* p) {
-  __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
-  return __bfloat1622float2(v);
+
+__device__ __forceinline__ float4 load_quad(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 load_quad(const __nv_bfloat16* p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
 }
 
 template <typename TD, int NV>
@@ -190,67 +208,98 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
     const int32_t* __restrict__ ci, const float* __restrict__ va,
     const float* __restrict__ vb, const float* __restrict__ scale,
     const TD* __restrict__ D, float* __restrict__ Wt) {
-  constexpr int TI = 32, TJ = 64, PAD = (NV == 1) ? 1 : 2;
-  __shared__ float tile[TI][TJ * NV + PAD];
+  constexpr int TI = 32, TJ = 128;
+  constexpr int RS = TJ * NV + (NV == 1 ? 1 : 2);   // tile row stride (floats)
+  __shared__ __align__(16) float tile[TI * RS];
+  __shared__ int rps[TI + 1];
   const int i0 = blockIdx.x * TI;
   const int j0 = blockIdx.y * TJ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const TD* dcol = D + j0 + 2 * lane;
+  for (int t = threadIdx.x; t < TI * RS; t += blockDim.x) tile[t] = 0.f;
+  if (threadIdx.x <= TI) rps[threadIdx.x] = rp[min(i0 + (int)threadIdx.x, n1)];
+  __syncthreads();
+  {
+    const int E0 = rps[0], len = rps[TI] - E0;
+    const int eb = E0 + (int)((int64_t)len * warp / 8);
+    const int ee = E0 + (int)((int64_t)len * (warp + 1) / 8);
+    const TD* dcol = D + j0 + 4 * lane;
+    int cur = -1;
+    float acc[4][NV];
 #pragma unroll
-  for (int rr = 0; rr < 4; ++rr) {
-    const int r = warp * 4 + rr;
-    const int i = i0 + r;
-    float a0[NV], a1[NV];
+    for (int c = 0; c < 4; ++c)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) a0[v] = a1[v] = 0.f;
-    if (i < n1) {
-      const int e0 = rp[i], e1 = rp[i + 1];
-      int e = e0;
-      for (; e + 2 <= e1; e += 2) {
-        const int k0 = ci[e], k1 = ci[e + 1];
-        float s0 = scale ? scale[k0] : 1.f, s1 = scale ? scale[k1] : 1.f;
-        const float2 d0 = load_pair(dcol + (int64_t)k0 * ldd);
-        const float2 d1 = load_pair(dcol + (int64_t)k1 * ldd);
-        float w0 = va[e] * s0, w1 = va[e + 1] * s1;
-        a0[0] += w0 * d0.x + w1 * d1.x;
-        a1[0] += w0 * d0.y + w1 * d1.y;
-        if (NV == 2) {
-          float x0 = vb[e] * s0, x1 = vb[e + 1] * s1;
-          a0[NV - 1] += x0 * d0.x + x1 * d1.x;
-          a1[NV - 1] += x0 * d0.y + x1 * d1.y;
+      for (int v = 0; v < NV; ++v) acc[c][v] = 0.f;
+    auto flush = [&]() {
+      if (cur >= 0) {
+        float* dst = tile + cur * RS + 4 * lane * NV;
+        if (rps[cur] < eb || rps[cur + 1] > ee) {   // row shared with another warp
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) atomicAdd(dst + c * NV + v, acc[c][v]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dst[c * NV + v] = acc[c][v];
         }
       }
-      for (; e < e1; ++e) {
-        const int k0 = ci[e];
-        float s0 = scale ? scale[k0] : 1.f;
-        const float2 d0 = load_pair(dcol + (int64_t)k0 * ldd);
-        float w0 = va[e] * s0;
-        a0[0] += w0 * d0.x;
-        a1[0] += w0 * d0.y;
-        if (NV == 2) {
-          float x0 = vb[e] * s0;
-          a0[NV - 1] += x0 * d0.x;
-          a1[NV - 1] += x0 * d0.y;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[c][v] = 0.f;
+    };
+    for (int base = eb; base < ee; base += 32) {
+      const int e = base + lane;
+      int k = 0, q = 0;
+      float wa = 0.f, wb = 0.f;
+      if (e < ee) {
+        k = ci[e];
+        const float sk = scale ? scale[k] : 1.f;
+        wa = va[e] * sk;
+        if constexpr (NV == 2) wb = vb[e] * sk;
+        q = seg_of<TI>(rps, e);
+      }
+      const int cnt = min(32, ee - base);
+      for (int u = 0; u < cnt; u += kGU) {
+        float4 d[kGU];
+#pragma unroll
+        for (int g = 0; g < kGU; ++g) {
+          const int kg = __shfl_sync(0xffffffffu, k, u + g);
+          if (u + g < cnt) d[g] = load_quad(dcol + (int64_t)kg * ldd);
+        }
+#pragma unroll
+        for (int g = 0; g < kGU; ++g) {
+          const int qg = __shfl_sync(0xffffffffu, q, u + g);
+          const float ag = __shfl_sync(0xffffffffu, wa, u + g);
+          const float bg = __shfl_sync(0xffffffffu, wb, u + g);
+          if (u + g < cnt) {
+            if (qg != cur) {
+              flush();
+              cur = qg;
+            }
+            const float dv[4] = {d[g].x, d[g].y, d[g].z, d[g].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              acc[c][0] = fmaf(ag, dv[c], acc[c][0]);
+              if constexpr (NV == 2) acc[c][NV - 1] = fmaf(bg, dv[c], acc[c][NV - 1]);
+            }
+          }
         }
       }
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      tile[r][(2 * lane) * NV + v] = a0[v];
-      tile[r][(2 * lane + 1) * NV + v] = a1[v];
-    }
+    flush();
   }
   __syncthreads();
   // transposed store: warp w writes columns c = w, w+8, ...; lane = row
-  using VT = typename VecF<NV>::T;
   for (int c = warp; c < TJ; c += 8) {
     const int j = j0 + c;
     if (j >= n2) break;
-    VT* dst = reinterpret_cast<VT*>(Wt + ((int64_t)j * ldw + i0) * NV);
     if constexpr (NV == 1) {
-      dst[lane] = tile[lane][c];
+      Wt[(int64_t)j * ldw + i0 + lane] = tile[lane * RS + c];
     } else {
-      dst[lane] = make_float2(tile[lane][c * 2], tile[lane][c * 2 + 1]);
+      reinterpret_cast<float2*>(Wt + ((int64_t)j * ldw + i0) * 2)[lane] =
+          make_float2(tile[lane * RS + 2 * c], tile[lane * RS + 2 * c + 1]);
     }
   }
 }
@@ -259,7 +308,7 @@ fa_status launch_spmm_left_T(const DevGraph& g1, int n2, int64_t ldd,
                              int64_t ldw, const float* va, const float* vb,
                              const float* scale, const void* D, bool d_bf16,
                              float* Wt, cudaStream_t s) {
-  dim3 grid((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 63) / 64));
+  dim3 grid((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 127) / 128));
   const bool two = vb != nullptr;
   if (d_bf16) {
     auto* Dp = static_cast<const __nv_bfloat16*>(D);
@@ -358,80 +407,138 @@ fa_status launch_spmm_right_prop(const DevGraph& g2, int n1, int64_t ldw,
 //   C   = C_node + lam_e Z_e - lam_n log max(Z_n, delta) + lam_a C_anc
 //   x   = -C/eps + (lam_p/eps) (log u_i + log K_prev_ij + log v_j)
 // stored as float32, plus the per-(row, 64-column tile) maximum of x.
-__device__ __forceinline__ void load8(const float* p, float (&k)[8]) {
-  float4 a = __ldg(reinterpret_cast<const float4*>(p));
-  float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
-  k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
-  k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
-}
-__device__ __forceinline__ void load8(const __nv_bfloat16* p, float (&k)[8]) {
-  uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
-  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float2 f = __bfloat1622float2(h[q]);
-    k[2 * q] = f.x;
-    k[2 * q + 1] = f.y;
-  }
-}
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename TK>
-__global__ void __launch_bounds__(256) k_spmm_right_cost(
+// CTA tile: 64 columns j x 64 rows i.  The tile's neighbour lists are one
+// contiguous CSR range [rp[j0], rp[j0+64]); it is split evenly over the 8
+// warps by edge count (not by column), so a hub column's gathers are shared
+// and the warps of a CTA finish together.  A warp loads 32 edges at a time
+// lane-parallel (column index, both weights times the scaling s_l, and the
+// output column found by binary search in the tile's row pointers), then
+// broadcasts them and keeps kGU gathers of W^T[l, i0:i0+64] (one float4 per
+// lane: rows 2 lane, 2 lane + 1, both value sets) in flight.  Sums of a
+// column are flushed into shared memory with atomics (a column can span two
+// warps); the epilogue then walks rows, lanes over columns, so the C_node,
+// K_prev and X rows are coalesced.  Shared tiles are XOR-swizzled by row so
+// both the flush (lanes over rows) and the epilogue (lanes over columns) are
+// free of bank conflicts up to 2 ways.
+constexpr int kRT = 64;    // rows per tile
+constexpr int kCT = 64;    // columns per tile
+
+__device__ __forceinline__ int sw_idx(int r, int c) { return r * kCT + (c ^ (r & 31)); }
+
+template <typename TK, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
     int n1, int n2, int64_t ldw, int64_t ldo, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const float* __restrict__ qa,
     const float* __restrict__ qb, const float* __restrict__ scale,
     const float* __restrict__ Wt, CostEpi ep) {
-  __shared__ float smax[8][32];
-  const int j0 = blockIdx.x * 64, i0 = blockIdx.y * 32;
+  __shared__ float ze_s[kRT * kCT];
+  __shared__ float zn_s[kRT * kCT];
+  __shared__ int rps[kCT + 1];
+  const int j0 = blockIdx.x * kCT, i0 = blockIdx.y * kRT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int jb = j0 + warp * 8;
-  float ze[8], zn[8];
+  for (int t = threadIdx.x; t < kRT * kCT; t += blockDim.x) {
+    ze_s[t] = 0.f;
+    zn_s[t] = 0.f;
+  }
+  if (threadIdx.x <= kCT) rps[threadIdx.x] = rp[min(j0 + (int)threadIdx.x, n2)];
+  __syncthreads();
+
+  // ---- gathers: Z_e[i, j] and Z_n[i, j] for rows 2 lane, 2 lane + 1
+  {
+    const int E0 = rps[0], len = rps[kCT] - E0;
+    const int eb = E0 + (int)((int64_t)len * warp / 8);
+    const int ee = E0 + (int)((int64_t)len * (warp + 1) / 8);
+    const int r0 = 2 * lane, r1 = 2 * lane + 1;
+    const float* wbase = Wt + (int64_t)(i0 + r0) * 2;
+    int cur = -1;
+    float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
+    auto flush = [&]() {
+      if (cur >= 0) {
+        atomicAdd(&ze_s[sw_idx(r0, cur)], a0);
+        atomicAdd(&zn_s[sw_idx(r0, cur)], b0);
+        atomicAdd(&ze_s[sw_idx(r1, cur)], a1);
+        atomicAdd(&zn_s[sw_idx(r1, cur)], b1);
+      }
+      a0 = b0 = a1 = b1 = 0.f;
+    };
+    for (int base = eb; base < ee; base += 32) {
+      const int e = base + lane;
+      int l = 0, q = 0;
+      float wa = 0.f, wb = 0.f;
+      if (e < ee) {
+        l = ci[e];
+        const float sl = scale ? scale[l] : 1.f;
+        wa = qa[e] * sl;
+        wb = qb[e] * sl;
+        q = seg_of<kCT>(rps, e);
+      }
+      const int cnt = min(32, ee - base);
+      for (int u = 0; u < cnt; u += kGU) {
+        float4 w[kGU];
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    right_accumulate<2>(jb + q, n2, ldw, i0, lane, rp, ci, qa, qb, scale, Wt,
-                        ze[q], zn[q]);
-  const int i = i0 + lane;
-  float mx = -INFINITY;
-  if (i < n1) {
-    float cn[8], kp[8];
-    load8(ep.C_node + (int64_t)i * ldo + jb, cn);
-    load8(static_cast<const TK*>(ep.K_prev) + (int64_t)i * ldo + jb, kp);
+        for (int k = 0; k < kGU; ++k) {
+          const int lk = __shfl_sync(0xffffffffu, l, u + k);
+          if (u + k < cnt)
+            w[k] = __ldg(reinterpret_cast<const float4*>(wbase + (int64_t)lk * ldw * 2));
+        }
+#pragma unroll
+        for (int k = 0; k < kGU; ++k) {
+          const int qk = __shfl_sync(0xffffffffu, q, u + k);
+          const float ak = __shfl_sync(0xffffffffu, wa, u + k);
+          const float bk = __shfl_sync(0xffffffffu, wb, u + k);
+          if (u + k < cnt) {
+            if (qk != cur) {
+              flush();
+              cur = qk;
+            }
+            a0 = fmaf(ak, w[k].x, a0);
+            b0 = fmaf(bk, w[k].y, b0);
+            a1 = fmaf(ak, w[k].z, a1);
+            b1 = fmaf(bk, w[k].w, b1);
+          }
+        }
+      }
+    }
+    flush();
+  }
+  __syncthreads();
+
+  // ---- epilogue: rows over warps, columns j0 + lane and j0 + 32 + lane
+  const float inv_eps = 1.0f / ep.eps;
+  const float prox = ep.lam_p * inv_eps;
+  const float c_off = -logf(ep.eps_anc);          // C_anc off the anchors
+  const float c_on = -logf(ep.eps_anc + 1.0f);    // C_anc on an anchor
+  const TK* Kp = static_cast<const TK*>(ep.K_prev);
+  for (int r = warp; r < kRT; r += 8) {
+    const int i = i0 + r;
+    if (i >= n1) break;
     const float lu = ep.log_u[i];
-    const float inv_eps = 1.0f / ep.eps;
-    const float prox = ep.lam_p * inv_eps;
-    const float c_off = -logf(ep.eps_anc);          // C_anc off the anchors
-    const float c_on = -logf(ep.eps_anc + 1.0f);    // C_anc on an anchor
     const int a0 = ep.anc_ptr[i], a1 = ep.anc_ptr[i + 1];
-    float x[8];
+    const int64_t row = (int64_t)i * ldo;
+    float mx = -INFINITY;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int j = jb + q;
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h, j = j0 + c;
+      float x = -INFINITY;
       if (j < n2) {
+        const int si = sw_idx(r, c);
         float canc = c_off;
         for (int a = a0; a < a1; ++a)
           if (ep.anc_col[a] == j) canc = c_on;
-        const float C = cn[q] + ep.lam_e * ze[q] -
-                        ep.lam_n * logf(fmaxf(zn[q], ep.delta)) +
-                        ep.lam_a * canc;
-        float xv = -C * inv_eps;
-        if (prox != 0.f) xv += prox * (lu + logf(kp[q]) + ep.log_v[j]);
-        x[q] = xv;
-        mx = fmaxf(mx, xv);
-      } else {
-        x[q] = -INFINITY;
+        const float C = ep.C_node[row + j] + ep.lam_e * ze_s[si] -
+                        ep.lam_n * logf(fmaxf(zn_s[si], ep.delta)) + ep.lam_a * canc;
+        x = -C * inv_eps;
+        if (prox != 0.f) x += prox * (lu + logf(to_f32(Kp[row + j])) + ep.log_v[j]);
+        mx = fmaxf(mx, x);
       }
+      ep.X[row + j] = x;
     }
-    float4* dst = reinterpret_cast<float4*>(ep.X + (int64_t)i * ldo + jb);
-    dst[0] = make_float4(x[0], x[1], x[2], x[3]);
-    dst[1] = make_float4(x[4], x[5], x[6], x[7]);
-  }
-  smax[warp][lane] = mx;
-  __syncthreads();
-  if (warp == 0) {
-    float m = smax[0][lane];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) m = fmaxf(m, smax[w][lane]);
-    if (i < n1) ep.rowmax_part[(int64_t)blockIdx.x * n1 + i] = m;
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) ep.rowmax_part[(int64_t)blockIdx.x * n1 + i] = mx;
   }
 }
 
@@ -440,13 +547,21 @@ fa_status launch_spmm_right_cost(const DevGraph& g2, int n1, int64_t ldw,
                                  const float* scale, const float* Wt,
                                  const CostEpi& ep, bool k_bf16,
                                  cudaStream_t s) {
-  dim3 grid((unsigned)(ldo / 64), (unsigned)((n1 + 31) / 32));
-  if (k_bf16)
-    k_spmm_right_cost<__nv_bfloat16><<<grid, 256, 0, s>>>(
-        n1, g2.n, ldw, ldo, g2.row_ptr, g2.col, qa, qb, scale, Wt, ep);
-  else
-    k_spmm_right_cost<float><<<grid, 256, 0, s>>>(
-        n1, g2.n, ldw, ldo, g2.row_ptr, g2.col, qa, qb, scale, Wt, ep);
+  // resident CTAs per SM the register budget is sized for: 3 (a few
+  // spilled registers) measured faster than 2 (none) on GB300 at 10k and 50k
+  static const int minb = [] {
+    const char* v = getenv("FA_PASSB_MINB");
+    return (v && atoi(v) == 2) ? 2 : 3;
+  }();
+  dim3 grid((unsigned)(ldo / kCT), (unsigned)((n1 + kRT - 1) / kRT));
+#define FA_PB(T, M) \
+  k_spmm_right_cost<T, M><<<grid, 256, 0, s>>>(n1, g2.n, ldw, ldo, g2.row_ptr, g2.col, qa, qb, scale, Wt, ep)
+  if (k_bf16) {
+    if (minb == 3) FA_PB(__nv_bfloat16, 3); else FA_PB(__nv_bfloat16, 2);
+  } else {
+    if (minb == 3) FA_PB(float, 3); else FA_PB(float, 2);
+  }
+#undef FA_PB
   FA_LAUNCHED("k_spmm_right_cost");
   return FA_OK;
 }
