@@ -149,6 +149,18 @@ __host__ __device__ constexpr int sweep_ctas_per_sm(int NT, int elems_per_thread
   return NT == 256 ? (elems_per_thread <= 16 ? 4 : 2) : 1;
 }
 
+// rs[r] = sum over CTAs c < QQ of xs[c * R + r], in CTA order
+template <int R, int QQ>
+__device__ __forceinline__ void sum_slots(const float* xs, float (&rs)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float a = 0.f;
+#pragma unroll
+    for (int c = 0; c < QQ; ++c) a += xs[c * R + r];
+    rs[r] = a;
+  }
+}
+
 template <typename TK, int S, int R, int NT>
 __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sweep(
     const TK* __restrict__ K, int64_t ld, int n1, int n2, int W, int NS,
@@ -206,10 +218,25 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
     }
   }
 
+  // 32-bit shared addresses of this thread's vectors in a ring row.  A
+  // vector past the slab edge (e0 >= W) is read at the slab's last vector
+  // instead: its v is 0, so it adds nothing to the row sums, and its column
+  // accumulators are never stored -- so no per-vector branch is needed.
+  uint32_t voff[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e0 = (s * NT + tid) * V;
+    voff[s] = (uint32_t)((e0 < W ? e0 : W - V) * (int)sizeof(TK));
+  }
+  const uint32_t ring_s = smem_u32(ring);
+  const uint32_t rowb = (uint32_t)W * sizeof(TK);
+  // vectors s < S-1 are inside the slab for every thread; the last one only
+  // for the first warps: skip it warp-uniformly where no lane has one
+  const bool last_ok = ((S - 1) * NT + warp * 32) * V < W;
+
   // producer: step t goes to stage t % NS
   int issued = 0;   // meaningful in thread 0 only
-  auto issue = [&](int t) {
-    const int stage = t % NS;
+  auto issue = [&](int t, int stage) {
     const int row0 = (g + t * G) * R;
     const int nrows = min(R, n1 - row0);
     const uint32_t mb = smem_u32(&full[stage]);
@@ -219,35 +246,39 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
                Kslab + (int64_t)(row0 + r) * ld, row_bytes, mb);
   };
   if (tid == 0) {
-    for (int t = 0; t < min(NS, T); ++t) issue(t);
+    for (int t = 0; t < min(NS, T); ++t) issue(t, t);
     issued = min(NS, T);
   }
 
   bool dead = false;
+  // ring stage and phase parity of step t, and the stage of step t-1
+  // (kept incrementally: no runtime division by NS in the loop)
+  int st_r = 0, st_c = 0;
+  uint32_t ph_r = 0;
   for (int t = 0; t <= T; ++t) {
     if (t < T) {
       // -------- partial row sums of step t
-      const int stage = t % NS;
-      if (!dead && !mbar_wait_bounded(smem_u32(&full[stage]), (uint32_t)((t / NS) & 1))) {
+      const int stage = st_r;
+      if (!dead && !mbar_wait_bounded(smem_u32(&full[stage]), ph_r)) {
         atomicOr(status, ST_TIMEOUT);
         s_timeout = 1;
       }
-      const TK* buf = ring + (size_t)stage * R * W;
       const int row0 = (g + t * G) * R;
       float* rb = red + (t & 1) * R * NW;
       // two independent paired accumulators per row (four FMA chains); the
       // R rows' shuffle trees are interleaved
+      const uint32_t sb = ring_s + (uint32_t)(stage * R) * rowb;
       float p[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         f2_t pa[2] = {pk2(0.f, 0.f), pk2(0.f, 0.f)};
         if (row0 + r < n1) {
+          const uint32_t rbase = sb + (uint32_t)r * rowb;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const int e0 = (s * NT + tid) * V;
-            if (e0 < W) {
+            if (s + 1 < S || last_ok) {
               f2_t f[V2];
-              pairs(lds128(buf + (size_t)r * W + e0), f, TK());
+              pairs(lds128a(rbase + voff[s]), f, TK());
 #pragma unroll
               for (int k = 0; k < V2; ++k) pa[k & 1] = ffma2(f[k], vv[s][k], pa[k & 1]);
             }
@@ -284,20 +315,35 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
         atomicOr(status, ST_TIMEOUT);
         s_timeout = 1;
       }
-      const int stage = tp % NS;
+      const int stage = st_c;
       const int row0 = (g + tp * G) * R;
-      const TK* buf = ring + (size_t)stage * R * W;
+      const uint32_t sb = ring_s + (uint32_t)(stage * R) * rowb;
       const float* rbp = red + (tp & 1) * R * NW;
+      // full row sums: the Q CTA partials of the exchange slot, summed in
+      // CTA order (fully unrolled per cluster size: independent loads at
+      // constant offsets; the same order in every CTA, so u is identical
+      // across the cluster)
+      float rsum[R];
+      if (Q > 1) {
+        const float* xs = xch + (tp % kNX) * kMaxQ * R;
+        switch (Q) {
+          case 2: sum_slots<R, 2>(xs, rsum); break;
+          case 4: sum_slots<R, 4>(xs, rsum); break;
+          case 8: sum_slots<R, 8>(xs, rsum); break;
+          default: sum_slots<R, 16>(xs, rsum); break;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          rsum[r] = 0.f;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) rsum[r] += rbp[r * NW + w];
+        }
+      }
       float u[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float rs = 0.f;
-        if (Q > 1) {
-          for (int qq = 0; qq < Q; ++qq) rs += xch[((tp % kNX) * kMaxQ + qq) * R + r];
-        } else {
-#pragma unroll
-          for (int w = 0; w < NW; ++w) rs += rbp[r * NW + w];
-        }
+        const float rs = rsum[r];
         const int row = row0 + r;
         float ur = 0.f;
         if (row < n1) {
@@ -315,12 +361,12 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
       for (int r = 0; r < R; ++r) {
         if (row0 + r < n1) {
           const f2_t u2 = pk2(u[r], u[r]);
+          const uint32_t rbase = sb + (uint32_t)r * rowb;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const int e0 = (s * NT + tid) * V;
-            if (e0 < W) {
+            if (s + 1 < S || last_ok) {
               f2_t f[V2];
-              pairs(lds128(buf + (size_t)r * W + e0), f, TK());
+              pairs(lds128a(rbase + voff[s]), f, TK());
 #pragma unroll
               for (int k = 0; k < V2; ++k) acc[s][k] = ffma2(u2, f[k], acc[s][k]);
             }
@@ -332,10 +378,15 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
       if (tid == 0) {
         if (Q > 1 && tp + kNX < T) mbar_expect_tx(smem_u32(&xbar[tp % kNX]), xch_bytes);
         if (!dead && tp + NS < T) {
-          issue(tp + NS);
+          issue(tp + NS, stage);
           issued = tp + NS + 1;
         }
       }
+    }
+    st_c = st_r;
+    if (++st_r == NS) {
+      st_r = 0;
+      ph_r ^= 1u;
     }
   }
   // after a timeout, wait (bounded) for copies still in flight into the ring

@@ -76,6 +76,16 @@ __device__ __forceinline__ uint4 lds128(const void* p) {
   return r;
 }
 
+// The same load from a 32-bit shared-memory address (no generic-to-shared
+// conversion; constant offsets fold into the instruction).
+__device__ __forceinline__ uint4 lds128a(uint32_t a) {
+  uint4 r;
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "r"(a));
+  return r;
+}
+
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -102,6 +112,20 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
+// The same test, letting the hardware suspend the thread (up to the hint,
+// in ns) until the phase completes instead of returning at once: waiting
+// warps then issue almost nothing.
+constexpr uint32_t kSuspendNs = 10000;
+__device__ __forceinline__ bool mbar_try_suspend(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity), "n"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait on an mbarrier phase: false after about 2 s (the caller then
 // records ST_TIMEOUT and stops depending on that data).
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -109,7 +133,7 @@ __device__ inline bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
   if (mbar_try(a, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < (1u << 28); ++it) {
-    if (mbar_try(a, parity)) return true;
+    if (mbar_try_suspend(a, parity)) return true;
     if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
   }
   return false;
