@@ -50,34 +50,53 @@ fa_status launch_exp_vec(int n, const float* x, float* y, cudaStream_t s) {
 
 // ------------------------------------------------------------ RWR (Alg. 1 L3)
 // Rout[i,:] = (1-beta) sum_k Abar[i,k] Rin[k,:]; the beta R^(0) term is
-// added afterwards by k_add_onehot.  One warp per row, float4 over columns.
+// added afterwards by k_add_onehot.  Column panels of 128 (one float4 per
+// lane), one warp per row, four neighbour gathers in flight; blockIdx.x runs
+// over rows first, so one panel of Rin (n x 128 floats) stays in L2 while
+// every row uses it instead of whole rows of Rin being re-read from HBM.
 __global__ void __launch_bounds__(256) k_rwr_step(
     int n, int L, int64_t ldr, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const float* __restrict__ val, float c,
     const float* __restrict__ Rin, float* __restrict__ Rout) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const int e0 = rp[warp], e1 = rp[warp + 1];
-  const int nv = (int)(ldr / 4);
-  float4* out = reinterpret_cast<float4*>(Rout + (int64_t)warp * ldr);
-  for (int c0 = lane; c0 < nv; c0 += 32) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int e = e0; e < e1; ++e) {
-      const float w = val[e];
-      const float4 r = __ldg(reinterpret_cast<const float4*>(Rin + (int64_t)ci[e] * ldr) + c0);
-      acc.x += w * r.x; acc.y += w * r.y; acc.z += w * r.z; acc.w += w * r.w;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int64_t nv = ldr / 4;
+  const int64_t c4 = (int64_t)blockIdx.y * 32 + lane;
+  if (row >= n || c4 >= nv) return;
+  const int e0 = rp[row], e1 = rp[row + 1];
+  const float4* Rv = reinterpret_cast<const float4*>(Rin) + c4;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  int e = e0;
+  for (; e + 4 <= e1; e += 4) {
+    float w[4];
+    float4 r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      w[u] = val[e + u];
+      r[u] = __ldg(Rv + (int64_t)ci[e + u] * nv);
     }
-    acc.x *= c; acc.y *= c; acc.z *= c; acc.w *= c;
-    out[c0] = acc;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc.x = fmaf(w[u], r[u].x, acc.x); acc.y = fmaf(w[u], r[u].y, acc.y);
+      acc.z = fmaf(w[u], r[u].z, acc.z); acc.w = fmaf(w[u], r[u].w, acc.w);
+    }
   }
+  for (; e < e1; ++e) {
+    const float w = val[e];
+    const float4 r = __ldg(Rv + (int64_t)ci[e] * nv);
+    acc.x = fmaf(w, r.x, acc.x); acc.y = fmaf(w, r.y, acc.y);
+    acc.z = fmaf(w, r.z, acc.z); acc.w = fmaf(w, r.w, acc.w);
+  }
+  acc.x *= c; acc.y *= c; acc.z *= c; acc.w *= c;
+  reinterpret_cast<float4*>(Rout + (int64_t)row * ldr)[c4] = acc;
 }
 
 fa_status launch_rwr_step(const DevGraph& g, int L, int64_t ldr, float beta,
                           const float* Rin, float* Rout, cudaStream_t s) {
-  int64_t threads = (int64_t)g.n * 32;
-  k_rwr_step<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-      g.n, L, ldr, g.row_ptr, g.col, g.val_row, 1.0f - beta, Rin, Rout);
+  if (g.n <= 0) return FA_OK;
+  dim3 grid((unsigned)((g.n + 7) / 8), (unsigned)((ldr / 4 + 31) / 32));
+  k_rwr_step<<<grid, 256, 0, s>>>(g.n, L, ldr, g.row_ptr, g.col, g.val_row, 1.0f - beta,
+                                  Rin, Rout);
   FA_LAUNCHED("k_rwr_step");
   return FA_OK;
 }
@@ -202,6 +221,17 @@ __device__ __forceinline__ float4 load_quad(const __nv_bfloat16* p) {
                      __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
 }
 
+// One CSR edge as a warp stages it: neighbour (gathered row), output row or
+// column within the tile, and the two weights times the neighbour's scaling.
+struct EdgeRec {
+  int nb, seg;
+  float wa, wb;
+};
+__device__ __forceinline__ EdgeRec lds_edge(const EdgeRec* p) {
+  const int4 v = *reinterpret_cast<const int4*>(p);
+  return EdgeRec{v.x, v.y, __int_as_float(v.z), __int_as_float(v.w)};
+}
+
 template <typename TD, int NV>
 __global__ void __launch_bounds__(256) k_spmm_left_T(
     int n1, int n2, int64_t ldd, int64_t ldw, const int32_t* __restrict__ rp,
@@ -209,13 +239,18 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
     const float* __restrict__ vb, const float* __restrict__ scale,
     const TD* __restrict__ D, float* __restrict__ Wt) {
   constexpr int TI = 32, TJ = 128;
-  constexpr int RS = TJ * NV + (NV == 1 ? 1 : 2);   // tile row stride (floats)
+  // tile row stride (floats): a multiple of 4 so a lane's 4 columns are
+  // 16-byte stores; the +4 (+2 words per 64-bit read) spreads the banks of
+  // the transposed read over a half warp
+  constexpr int RS = TJ * NV + 4;
   __shared__ __align__(16) float tile[TI * RS];
+  __shared__ __align__(16) EdgeRec edges[8][32];
   __shared__ int rps[TI + 1];
   const int i0 = blockIdx.x * TI;
   const int j0 = blockIdx.y * TJ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int t = threadIdx.x; t < TI * RS; t += blockDim.x) tile[t] = 0.f;
+  for (int t = threadIdx.x; t < TI * RS / 4; t += blockDim.x)
+    reinterpret_cast<float4*>(tile)[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (threadIdx.x <= TI) rps[threadIdx.x] = rp[min(i0 + (int)threadIdx.x, n1)];
   __syncthreads();
   {
@@ -223,6 +258,7 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
     const int eb = E0 + (int)((int64_t)len * warp / 8);
     const int ee = E0 + (int)((int64_t)len * (warp + 1) / 8);
     const TD* dcol = D + j0 + 4 * lane;
+    EdgeRec* my = edges[warp];
     int cur = -1;
     float acc[4][NV];
 #pragma unroll
@@ -237,11 +273,11 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
           for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int v = 0; v < NV; ++v) atomicAdd(dst + c * NV + v, acc[c][v]);
+        } else if constexpr (NV == 2) {
+          reinterpret_cast<float4*>(dst)[0] = make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]);
+          reinterpret_cast<float4*>(dst)[1] = make_float4(acc[2][0], acc[2][1], acc[3][0], acc[3][1]);
         } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) dst[c * NV + v] = acc[c][v];
+          reinterpret_cast<float4*>(dst)[0] = make_float4(acc[0][0], acc[1][0], acc[2][0], acc[3][0]);
         }
       }
 #pragma unroll
@@ -251,42 +287,36 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
     };
     for (int base = eb; base < ee; base += 32) {
       const int e = base + lane;
-      int k = 0, q = 0;
-      float wa = 0.f, wb = 0.f;
       if (e < ee) {
-        k = ci[e];
+        const int k = ci[e];
         const float sk = scale ? scale[k] : 1.f;
-        wa = va[e] * sk;
-        if constexpr (NV == 2) wb = vb[e] * sk;
-        q = seg_of<TI>(rps, e);
+        my[lane] = EdgeRec{k, seg_of<TI>(rps, e), va[e] * sk, NV == 2 ? vb[e] * sk : 0.f};
       }
+      __syncwarp();
       const int cnt = min(32, ee - base);
       for (int u = 0; u < cnt; u += kGU) {
         float4 d[kGU];
 #pragma unroll
-        for (int g = 0; g < kGU; ++g) {
-          const int kg = __shfl_sync(0xffffffffu, k, u + g);
-          if (u + g < cnt) d[g] = load_quad(dcol + (int64_t)kg * ldd);
-        }
+        for (int g = 0; g < kGU; ++g)
+          if (u + g < cnt) d[g] = load_quad(dcol + (int64_t)my[u + g].nb * ldd);
 #pragma unroll
         for (int g = 0; g < kGU; ++g) {
-          const int qg = __shfl_sync(0xffffffffu, q, u + g);
-          const float ag = __shfl_sync(0xffffffffu, wa, u + g);
-          const float bg = __shfl_sync(0xffffffffu, wb, u + g);
           if (u + g < cnt) {
-            if (qg != cur) {
+            const EdgeRec er = lds_edge(&my[u + g]);
+            if (er.seg != cur) {
               flush();
-              cur = qg;
+              cur = er.seg;
             }
             const float dv[4] = {d[g].x, d[g].y, d[g].z, d[g].w};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-              acc[c][0] = fmaf(ag, dv[c], acc[c][0]);
-              if constexpr (NV == 2) acc[c][NV - 1] = fmaf(bg, dv[c], acc[c][NV - 1]);
+              acc[c][0] = fmaf(er.wa, dv[c], acc[c][0]);
+              if constexpr (NV == 2) acc[c][NV - 1] = fmaf(er.wb, dv[c], acc[c][NV - 1]);
             }
           }
         }
       }
+      __syncwarp();
     }
     flush();
   }
@@ -299,7 +329,105 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
       Wt[(int64_t)j * ldw + i0 + lane] = tile[lane * RS + c];
     } else {
       reinterpret_cast<float2*>(Wt + ((int64_t)j * ldw + i0) * 2)[lane] =
-          make_float2(tile[lane * RS + 2 * c], tile[lane * RS + 2 * c + 1]);
+          *reinterpret_cast<const float2*>(&tile[lane * RS + 2 * c]);
+    }
+  }
+}
+
+// Row-per-warp form of the left SpMM: tile 32 rows x 64 columns, warp w
+// owns rows 4w..4w+3 (lane l: columns 2l, 2l+1), four neighbour gathers in
+// flight, transposed store through shared memory.  Used for Pass A's two
+// value sets; FA_PASSA_ROWS=0/1 forces either form.
+template <int NV> struct VecF;
+template <> struct VecF<1> { using T = float; };
+template <> struct VecF<2> { using T = float2; };
+
+__device__ __forceinline__ float2 load_pair(const float* p) {
+  return __ldg(reinterpret_cast<const float2*>(p));
+}
+__device__ __forceinline__ float2 load_pair(const __nv_bfloat16* p) {
+  __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
+  return __bfloat1622float2(v);
+}
+
+template <typename TD, int NV>
+__global__ void __launch_bounds__(256) k_spmm_left_T_rows(
+    int n1, int n2, int64_t ldd, int64_t ldw, const int32_t* __restrict__ rp,
+    const int32_t* __restrict__ ci, const float* __restrict__ va,
+    const float* __restrict__ vb, const float* __restrict__ scale,
+    const TD* __restrict__ D, float* __restrict__ Wt) {
+  constexpr int TI = 32, TJ = 64, PAD = (NV == 1) ? 1 : 2;
+  __shared__ float tile[TI][TJ * NV + PAD];
+  const int i0 = blockIdx.x * TI;
+  const int j0 = blockIdx.y * TJ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TD* dcol = D + j0 + 2 * lane;
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) {
+    const int r = warp * 4 + rr;
+    const int i = i0 + r;
+    float a0[NV], a1[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a0[v] = a1[v] = 0.f;
+    if (i < n1) {
+      const int e0 = rp[i], e1 = rp[i + 1];
+      int e = e0;
+      // four neighbour gathers in flight
+      for (; e + 4 <= e1; e += 4) {
+        int k[4];
+        float2 d[4];
+        float w[4], x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k[u] = ci[e + u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u] = load_pair(dcol + (int64_t)k[u] * ldd);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float su = scale ? scale[k[u]] : 1.f;
+          w[u] = va[e + u] * su;
+          x[u] = NV == 2 ? vb[e + u] * su : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a0[0] = fmaf(w[u], d[u].x, a0[0]);
+          a1[0] = fmaf(w[u], d[u].y, a1[0]);
+          if (NV == 2) {
+            a0[NV - 1] = fmaf(x[u], d[u].x, a0[NV - 1]);
+            a1[NV - 1] = fmaf(x[u], d[u].y, a1[NV - 1]);
+          }
+        }
+      }
+      for (; e < e1; ++e) {
+        const int k0 = ci[e];
+        float s0 = scale ? scale[k0] : 1.f;
+        const float2 d0 = load_pair(dcol + (int64_t)k0 * ldd);
+        float w0 = va[e] * s0;
+        a0[0] = fmaf(w0, d0.x, a0[0]);
+        a1[0] = fmaf(w0, d0.y, a1[0]);
+        if (NV == 2) {
+          float x0 = vb[e] * s0;
+          a0[NV - 1] = fmaf(x0, d0.x, a0[NV - 1]);
+          a1[NV - 1] = fmaf(x0, d0.y, a1[NV - 1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      tile[r][(2 * lane) * NV + v] = a0[v];
+      tile[r][(2 * lane + 1) * NV + v] = a1[v];
+    }
+  }
+  __syncthreads();
+  // transposed store: warp w writes columns c = w, w+8, ...; lane = row
+  using VT = typename VecF<NV>::T;
+  for (int c = warp; c < TJ; c += 8) {
+    const int j = j0 + c;
+    if (j >= n2) break;
+    VT* dst = reinterpret_cast<VT*>(Wt + ((int64_t)j * ldw + i0) * NV);
+    if constexpr (NV == 1) {
+      dst[lane] = tile[lane][c];
+    } else {
+      dst[lane] = make_float2(tile[lane][c * 2], tile[lane][c * 2 + 1]);
     }
   }
 }
@@ -308,8 +436,28 @@ fa_status launch_spmm_left_T(const DevGraph& g1, int n2, int64_t ldd,
                              int64_t ldw, const float* va, const float* vb,
                              const float* scale, const void* D, bool d_bf16,
                              float* Wt, cudaStream_t s) {
-  dim3 grid((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 127) / 128));
   const bool two = vb != nullptr;
+  // measured at 50k on GB300: the row-per-warp form is faster for the two
+  // value sets of Pass A in BF16 (17 vs 22 ms), equal for propagation
+  static const int form = [] {
+    const char* v = getenv("FA_PASSA_ROWS");
+    return v ? atoi(v) : -1;
+  }();
+  if (form == 1 || (form != 0 && two)) {
+    dim3 g2d((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 63) / 64));
+    if (d_bf16) {
+      auto* Dp = static_cast<const __nv_bfloat16*>(D);
+      if (two) k_spmm_left_T_rows<__nv_bfloat16, 2><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+      else     k_spmm_left_T_rows<__nv_bfloat16, 1><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+    } else {
+      auto* Dp = static_cast<const float*>(D);
+      if (two) k_spmm_left_T_rows<float, 2><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+      else     k_spmm_left_T_rows<float, 1><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+    }
+    FA_LAUNCHED("k_spmm_left_T_rows");
+    return FA_OK;
+  }
+  dim3 grid((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 127) / 128));
   if (d_bf16) {
     auto* Dp = static_cast<const __nv_bfloat16*>(D);
     if (two) k_spmm_left_T<__nv_bfloat16, 2><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
@@ -436,6 +584,7 @@ __global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
     const float* __restrict__ Wt, CostEpi ep) {
   __shared__ float ze_s[kRT * kCT];
   __shared__ float zn_s[kRT * kCT];
+  __shared__ __align__(16) EdgeRec edges[8][32];
   __shared__ int rps[kCT + 1];
   const int j0 = blockIdx.x * kCT, i0 = blockIdx.y * kRT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -464,43 +613,38 @@ __global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
       }
       a0 = b0 = a1 = b1 = 0.f;
     };
+    EdgeRec* my = edges[warp];
     for (int base = eb; base < ee; base += 32) {
       const int e = base + lane;
-      int l = 0, q = 0;
-      float wa = 0.f, wb = 0.f;
       if (e < ee) {
-        l = ci[e];
+        const int l = ci[e];
         const float sl = scale ? scale[l] : 1.f;
-        wa = qa[e] * sl;
-        wb = qb[e] * sl;
-        q = seg_of<kCT>(rps, e);
+        my[lane] = EdgeRec{l, seg_of<kCT>(rps, e), qa[e] * sl, qb[e] * sl};
       }
+      __syncwarp();
       const int cnt = min(32, ee - base);
       for (int u = 0; u < cnt; u += kGU) {
         float4 w[kGU];
 #pragma unroll
-        for (int k = 0; k < kGU; ++k) {
-          const int lk = __shfl_sync(0xffffffffu, l, u + k);
+        for (int k = 0; k < kGU; ++k)
           if (u + k < cnt)
-            w[k] = __ldg(reinterpret_cast<const float4*>(wbase + (int64_t)lk * ldw * 2));
-        }
+            w[k] = __ldg(reinterpret_cast<const float4*>(wbase + (int64_t)my[u + k].nb * ldw * 2));
 #pragma unroll
         for (int k = 0; k < kGU; ++k) {
-          const int qk = __shfl_sync(0xffffffffu, q, u + k);
-          const float ak = __shfl_sync(0xffffffffu, wa, u + k);
-          const float bk = __shfl_sync(0xffffffffu, wb, u + k);
           if (u + k < cnt) {
-            if (qk != cur) {
+            const EdgeRec er = lds_edge(&my[u + k]);
+            if (er.seg != cur) {
               flush();
-              cur = qk;
+              cur = er.seg;
             }
-            a0 = fmaf(ak, w[k].x, a0);
-            b0 = fmaf(bk, w[k].y, b0);
-            a1 = fmaf(ak, w[k].z, a1);
-            b1 = fmaf(bk, w[k].w, b1);
+            a0 = fmaf(er.wa, w[k].x, a0);
+            b0 = fmaf(er.wb, w[k].y, b0);
+            a1 = fmaf(er.wa, w[k].z, a1);
+            b1 = fmaf(er.wb, w[k].w, b1);
           }
         }
       }
+      __syncwarp();
     }
     flush();
   }
