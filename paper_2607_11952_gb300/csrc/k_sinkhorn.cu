@@ -152,12 +152,22 @@ __host__ __device__ constexpr int sweep_ctas_per_sm(int NT, int elems_per_thread
 // rs[r] = sum over CTAs c < QQ of xs[c * R + r], in CTA order
 template <int R, int QQ>
 __device__ __forceinline__ void sum_slots(const float* xs, float (&rs)[R]) {
+  if constexpr (R == 2) {
+    // both rows of a CTA's slot in one 8-byte load, summed as a pair
+    f2_t a = *reinterpret_cast<const f2_t*>(xs);
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    float a = 0.f;
+    for (int c = 1; c < QQ; ++c) a = fadd2(a, *reinterpret_cast<const f2_t*>(xs + 2 * c));
+    const float2 f = upk2(a);
+    rs[0] = f.x;
+    rs[1 % R] = f.y;
+  } else {
 #pragma unroll
-    for (int c = 0; c < QQ; ++c) a += xs[c * R + r];
-    rs[r] = a;
+    for (int r = 0; r < R; ++r) {
+      float a = 0.f;
+#pragma unroll
+      for (int c = 0; c < QQ; ++c) a += xs[c * R + r];
+      rs[r] = a;
+    }
   }
 }
 
@@ -288,9 +298,24 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
         p[r] = (a.x + a.y) + (b.x + b.y);
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      if constexpr (R == 2) {
+        // the two rows' butterfly sums as one paired add per level
+        f2_t pp = pk2(p[0], p[1]);
 #pragma unroll
-        for (int r = 0; r < R; ++r) p[r] += __shfl_xor_sync(0xffffffffu, p[r], o);
+        for (int o = 16; o > 0; o >>= 1) {
+          const float2 h = upk2(pp);
+          pp = fadd2(pp, pk2(__shfl_xor_sync(0xffffffffu, h.x, o),
+                             __shfl_xor_sync(0xffffffffu, h.y, o)));
+        }
+        const float2 h = upk2(pp);
+        p[0] = h.x;
+        p[1 % R] = h.y;
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) p[r] += __shfl_xor_sync(0xffffffffu, p[r], o);
+        }
       }
       if (lane == 0) {
 #pragma unroll
