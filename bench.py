@@ -3,13 +3,15 @@
 Workload: the 50k-node Chung-Lu pair (exponent 2.1, mean degree 10, 15% edge
 noise, 128-dim attributes, 5% anchors), seeded synthetic data.  One step is
 an alignment with inputs resident in HBM: Phase 1 (RWR, SDDMM,
-node-cost GEMM, propagation), then OUTER (default 4) outer iterations of Phase 2
-(Pass A, Pass B + Gibbs kernel) and Phase 3 (fused Sinkhorn sweeps until the
-L1 marginal error is <= 1e-4, checked every 5 sweeps), then the top-10
-read-out.  The metric is the step time (lower is better).  The Gibbs kernel
-(5 GB in BF16) is far larger than L2, so no flush is needed between steps.
+node-cost GEMM, propagation), then the workload's 30 outer iterations of
+Phase 2 (Pass A, Pass B + Gibbs kernel) and Phase 3 (fused Sinkhorn sweeps,
+learned warm start, until the L1 marginal error is <= 1e-4, checked every 5
+sweeps), then the top-10 read-out.  The metric is the step time (lower is
+better); the same alignment in plain FP32 with a cold start is timed once
+beside it.  The Gibbs kernel (5 GB in BF16) is far larger than L2, so no
+flush is needed between steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--outer T] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the 5k-node pair with the same generator
@@ -32,6 +34,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "50k-node time to 1e-4 marginal err, learned+BF16 vs plain FP32; sweep HBM GB/s"
+
+# Sinkhorn iterations the plain method (FP32 storage, cold start) needs on a
+# workload, as measured on GB300 by this script's FP32 comparison; the
+# reference arm scales the oracle's per-iteration time by it.
+PLAIN_SWEEPS = {("cl50k", 30): 61790, ("cl50k", 4): 1190}
 
 
 def _peaks():
@@ -182,7 +189,6 @@ def run_ours(args):
     if args.compare_fp32 and args.dtype != "f32":
         al32 = api.Aligner(G1, G2, api.Params(dtype="f32"), device=dev)
         al32.set_timing(True)
-        step(al32)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r32 = []
@@ -207,13 +213,7 @@ def run_ours(args):
             "ms_per_step": round(ms, 3), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic (seeded Chung-Lu pair; no dataset)",
-            "config": {"workload": f"{args.config}: Chung-Lu n1=n2={g.n1}, gamma=2.1, "
-                                   f"avg deg 10, 15% noise, d=128, 5% anchors; "
-                                   f"Phase 1 + {args.outer} outer x Sinkhorn to "
-                                   f"{args.tol:g} (check every {args.check_every}) + top-10",
-                       "n1": g.n1, "n2": g.n2, "outer": args.outer, "tol": args.tol,
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (K is 5 GB), no flush"},
+            "config": _config(args, world),
             "sweeps_per_step": total_sweeps / args.steps,
             "warm_start": args.warm,
             "hits@1": hits["hits@1"], "mrr": hits["mrr"],
@@ -235,13 +235,30 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+SWEEP_SOURCES = ("paper_2607_11952_gb300/csrc/k_sinkhorn.cu",
+                 "paper_2607_11952_gb300/csrc/sweep_dev.cuh")
+
+
+def sweep_source_hash():
+    """sha256 of the sweep kernel's source files, stored with the ncu
+    counters so a traffic figure is only reported for the kernel it was
+    taken from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
 def _ncu_traffic(args):
     """DRAM bytes per k_sweep launch from the committed ncu summary, if it
-    was taken for the current kernel and dtype (None otherwise)."""
+    was taken for the current kernel source and dtype (None otherwise)."""
     p = os.path.join(ROOT, "profiles", "k_sweep_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
+    if d.get("source_sha256") != sweep_source_hash():
+        return None
     e = d.get(args.dtype)
     return e.get("dram_bytes_per_launch_full_size") if e else None
 
@@ -258,7 +275,7 @@ def _e2e(args, g, dev, api, model):
     X2h = torch.from_numpy(g.X2).pin_memory()
     h2d = X1h.numel() * 4 + X2h.numel() * 4 + (g.edges1.size + g.edges2.size) * 4 + g.anchors.size * 4
     times = []
-    for k in range(2):
+    for k in range(args.e2e_runs):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G1, G2 = api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2)
@@ -278,7 +295,7 @@ def _e2e(args, g, dev, api, model):
         al.close()
         G1.close()
         G2.close()
-    return {"value": round(min(times[1:] or times), 3), "unit": "ms",
+    return {"value": round(min(times[1:] or times), 3), "unit": "ms", "runs": len(times),
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes)}
 
 
@@ -328,6 +345,26 @@ def _cpu_baseline(args, sweeps):
                       f"elementwise work is single-threaded, BLAS uses all cores"}
 
 
+def _config(args, world):
+    """The workload both arms report (same keys and values)."""
+    c = _synth_config(args.config)
+    n1 = c["n"]
+    n2 = c.get("keep") or n1
+    return {"workload": f"{args.config}: Chung-Lu n1={n1} n2={n2}, gamma={c['gamma']}, "
+                        f"avg deg {c['avg_deg']:g}, {100 * c['frac_del']:g}% edge noise, "
+                        f"d={c['d']}, {100 * c['anchor_frac']:g}% anchors; Phase 1 + "
+                        f"{args.outer} outer x Sinkhorn to {args.tol:g} (check every "
+                        f"{args.check_every}) + top-10",
+            "n1": n1, "n2": n2, "outer": args.outer, "tol": args.tol,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (K is 5 GB), no flush"}
+
+
+def _synth_config(name):
+    from paper_2607_11952_gb300 import synth
+    return synth.CONFIGS[name]
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -344,14 +381,17 @@ def run_reference(args):
         "metric": METRIC, "value": round(v, 1), "unit": "ms", "impl": "reference",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.config}: Phase 1 + {args.outer} outer iterations "
-                               f"with {args.ref_sweeps} Sinkhorn iterations in total, "
-                               f"estimated from the FP64 oracle at n={g.n1} scaled to n=50k"},
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Chung-Lu pair; no dataset)",
+        "config": _config(args, world),
         "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": os.cpu_count(),
                          "kind": "oracle",
-                         "sample": f"Phase 1, Phase 2 and Sinkhorn iterations timed at "
-                                   f"n={g.n1}, scaled"},
+                         "sample": f"FP64 oracle, cold start: Phase 1, Phase 2 and Sinkhorn "
+                                   f"iterations timed on the n={g.n1} pair with the "
+                                   f"workload's generator parameters, scaled to n=50k "
+                                   f"(n^3 Phase 1, n^2 per outer and per Sinkhorn "
+                                   f"iteration) for {args.outer} outer iterations and "
+                                   f"{args.ref_sweeps} Sinkhorn iterations (the plain "
+                                   f"method's count on this workload)"},
         "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -361,22 +401,31 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cl50k")
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "f32"])
-    ap.add_argument("--outer", type=int, default=4)
+    # outer iterations per step (default: the workload's own count, 30 at 50k)
+    ap.add_argument("--outer", type=int, default=None)
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--check-every", type=int, default=5)
     ap.add_argument("--max-sweeps", type=int, default=5000)
-    # Sinkhorn iterations of one step on the GPU (measured), for --impl reference
-    ap.add_argument("--ref-sweeps", type=int, default=1190)
+    # Sinkhorn iterations of the plain method (FP32, cold start) in one step,
+    # for --impl reference (default: the count measured on the GPU for the
+    # default workload)
+    ap.add_argument("--ref-sweeps", type=int, default=None)
+    ap.add_argument("--e2e-runs", type=int, default=1)
     ap.add_argument("--no-fp32", dest="compare_fp32", action="store_false")
     ap.add_argument("--warm", default="learned", choices=["learned", "prev", "cold"])
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
+    if args.outer is None:
+        args.outer = _synth_config(args.config)["outer"]
+    if args.ref_sweeps is None:
+        args.ref_sweeps = PLAIN_SWEEPS.get((args.config, args.outer), 0) or \
+            int(round(2060 * args.outer))
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
