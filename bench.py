@@ -95,6 +95,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def replica_seed(config: str, rank: int) -> int:
+    """Rank r of a replicas run aligns its own pair: the workload's seed + r."""
+    from paper_2607_11952_gb300 import synth
+    return synth.CONFIGS[config]["seed"] + rank
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The job's step time: the slowest rank's (all ranks run the same
+    number of independent alignments, so the whole job's time per step is
+    the maximum)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -114,7 +133,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     # independent replicas: rank r aligns its own pair (seed + r)
-    g = synth.config_pair(args.config, seed=synth.CONFIGS[args.config]["seed"] + rank)
+    g = synth.config_pair(args.config, seed=replica_seed(args.config, rank))
     G1, G2 = api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2)
     params = api.Params(dtype=args.dtype)
     al = api.Aligner(G1, G2, params, device=dev)
@@ -168,10 +187,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = L.fa_kernel_launch_count() - launches0
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     hits = al.hits_mrr(g.test_pairs)
 
     # dominant kernel: the fused sweep; time per launch from CUDA events

@@ -172,3 +172,34 @@ def test_learned_and_cold_reach_the_same_plan_50k(setup):
         assert d <= 1e-3
     finally:
         al.close()
+
+
+def test_largest_uneven_pair_100k_by_80k():
+    """The largest workload (G2 an induced 80k subgraph of a 100k graph,
+    256-dim attributes, 2% anchors): Phase 1, one outer iteration and
+    Sinkhorn to 1e-4 with BF16 storage; row and column marginals of the
+    unequal masses mu = 1/n1, nu = 1/n2 recomputed in float64."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    g = synth.config_pair("cl100k")
+    assert (g.n1, g.n2) == (100_000, 80_000)
+    al = _aligner(g, "bf16")
+    try:
+        al.node_cost(g.X1, g.X2, g.anchors)
+        al.plan_init()
+        al.align_iter()
+        it, err, st = al.sinkhorn(5000, 1e-4, 5)
+        torch.cuda.synchronize()
+        rsum, csum = _marginals(al)
+        row_err = float((rsum - 1.0 / al.n1).abs().sum())
+        col_err = float((csum - 1.0 / al.n2).abs().sum())
+        print(f"100k x 80k: {it} sweeps, reported {err:.3e}, column {col_err:.3e}, row {row_err:.3e}")
+        assert st == 0
+        assert row_err <= 1e-5
+        assert abs(err - col_err) <= 1e-3 * col_err + ERR_FLOOR
+        assert col_err <= 1e-4 + ERR_FLOOR
+        assert bool(torch.isfinite(al.log_u).all()) and bool(torch.isfinite(al.log_v).all())
+    finally:
+        al.close()
