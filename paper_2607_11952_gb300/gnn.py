@@ -1,12 +1,18 @@
 """Learned warm start of the Sinkhorn solves (not part of the paper).
 
-A 2-layer graph network on the column graph G2 (hidden width 64, BF16
-weights) predicts, for the solve of one outer iteration, the correction
-y = log v* - log v1 between the converged column scaling v* and the cold
-first column update v1 that fa_align_iter leaves in ``log_v``.  The solve
-then starts from ``warm_log_v = log v1 + prediction``; the plain cold start
-(no warm start) stays available and is the reference the model is judged
-against.  The model's forward, backward and Adam kernels are the library's
+Each solve of an outer iteration starts from the cold first column update
+v1 that fa_align_iter leaves in ``log_v``; its converged column scaling v*
+differs from it by the correction c = log v* - log v1.  Consecutive outer
+iterations have similar corrections, so the warm start is
+
+    warm_log_v = log v1 + c_prev + clamp(f(features)),
+
+where c_prev is the previous solve's correction (0 at the first) and f, a
+2-layer graph network on the column graph G2 (hidden width 64, BF16
+weights), predicts the change of the correction, c - c_prev.  With f = 0
+this is the "previous correction" warm start; the network learns what that
+misses.  The plain cold start (no warm start) stays available and is the
+reference the model is judged against.  The model's forward, backward and Adam kernels are the library's
 (fa_gnn_*); this module only moves tensors and decides what to call.
 
 Training data are the method's own solves: Chung-Lu pairs with n uniform in
@@ -104,12 +110,12 @@ class WarmStarter:
     """Warm-start protocol for the solves of one alignment.
 
     mode "cold":    no warm start (fa_sinkhorn's first b update uses v1).
-    mode "prev":    warm_log_v = log v1 + the previous solve's correction.
-    mode "learned": warm_log_v = log v1 + model(features).
+    mode "prev":    warm_log_v = log v1 + c_prev (the previous solve's correction).
+    mode "learned": warm_log_v = log v1 + c_prev + clamp(model(features)).
     Call ``before_solve`` right after fa_align_iter and ``after_solve``
     after fa_sinkhorn, or ``solve`` for both with the cold-start fallback."""
 
-    MAX_CORR = 20.0     # bound on a predicted correction (natural-log units)
+    MAX_CORR = 20.0     # bound on a predicted change of the correction (log units)
 
     def __init__(self, aligner: api.Aligner, mode: str = "learned",
                  model: WarmStartModel | None = None):
@@ -121,6 +127,7 @@ class WarmStarter:
         self.log_v1 = torch.empty(n2, dtype=torch.float32, device=dev)
         self.corr = torch.zeros(n2, dtype=torch.float32, device=dev)
         self.warm = torch.empty(n2, dtype=torch.float32, device=dev)
+        self.base = torch.empty(n2, dtype=torch.float32, device=dev)
         self.F = torch.empty((n2, FIN), dtype=torch.float32, device=dev)
 
     def before_solve(self):
@@ -132,7 +139,9 @@ class WarmStarter:
             return self.warm
         self.model.features(self.al.g2, self.log_v1, self.corr, self.F)
         pred = self.model.predict(self.al.g2, self.F)
-        L.fa_gnn_warm_start(self.al.n2, self.log_v1, pred, self.MAX_CORR, self.warm)
+        # base = log v1 + c_prev, then warm = base + clamp(pred)
+        L.fa_vec_axpby(self.al.n2, 1.0, self.log_v1, 1.0, self.corr, self.base)
+        L.fa_gnn_warm_start(self.al.n2, self.base, pred, self.MAX_CORR, self.warm)
         return self.warm
 
     def after_solve(self):
@@ -160,7 +169,7 @@ class WarmStarter:
 class Sample:
     graph: api.Graph          # column graph G2 (kept alive)
     F: torch.Tensor           # n x 3 features
-    y: torch.Tensor           # n target corrections
+    y: torch.Tensor           # n targets: change of the correction, c - c_prev
 
 
 def training_pair(k: int, seed: int) -> synth.GraphPair:
@@ -178,23 +187,27 @@ def training_pair(k: int, seed: int) -> synth.GraphPair:
 def generate_solves(n_pairs: int, outer: int, seed: int = 7, tol: float = 1e-5,
                     max_sweeps: int = 20000, dtype: str = "f32", log=None):
     """Run the method on training pairs and record, for every outer
-    iteration, the features and the converged correction of its solve."""
+    iteration, the features and the change of the converged correction
+    c - c_prev.  The solves start from the previous correction (the
+    converged potentials do not depend on the start, only the number of
+    iterations does)."""
     samples = []
     model = WarmStartModel(seed=seed)            # only for its feature kernel
     for k in range(n_pairs):
         g = training_pair(k, seed)
         G1, G2 = api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2)
         al = api.Aligner(G1, G2, api.Params(dtype=dtype))
-        ws = WarmStarter(al, "cold")
+        ws = WarmStarter(al, "prev")
         al.node_cost(g.X1, g.X2, g.anchors)
         al.plan_init()
         for t in range(outer):
             al.align_iter()
-            ws.before_solve()
+            warm = ws.before_solve()
             F = model.features(G2, ws.log_v1, ws.corr)
-            al.sinkhorn(max_sweeps, tol, 10)
+            c_prev = ws.corr.clone()
+            al.sinkhorn(max_sweeps, tol, 10, warm)
             ws.after_solve()
-            samples.append(Sample(G2, F.clone(), ws.corr.clone()))
+            samples.append(Sample(G2, F.clone(), ws.corr - c_prev))
         al.close()
         if log and (k + 1) % 25 == 0:
             log(f"generated {len(samples)} solves from {k + 1} pairs")
