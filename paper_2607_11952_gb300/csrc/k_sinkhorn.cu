@@ -297,7 +297,6 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
         const float2 a = upk2(pa[0]), b = upk2(pa[1]);
         p[r] = (a.x + a.y) + (b.x + b.y);
       }
-#pragma unroll
       if constexpr (R == 2) {
         // the two rows' butterfly sums as one paired add per level
         f2_t pp = pk2(p[0], p[1]);
