@@ -16,7 +16,7 @@
  *   return without synchronising, except where they return a host scalar
  *   (fa_sinkhorn), which synchronises that stream only.
  * - Dense n1 x n2 matrices are row-major with a padded leading dimension
- *   ld = fa_ctx_ld(ctx) >= n2 (a multiple of 64 elements).  Padding columns
+ *   ld = fa_ctx_ld(ctx) >= n2 (a multiple of 128 elements).  Padding columns
  *   of the Gibbs kernel K are written as 0 and must stay 0.
  * - The transport plan is held implicitly as
  *       T_ij = exp(log_u_i) * K_ij * exp(log_v_j)
