@@ -267,6 +267,22 @@ fa_status fa_gnn_warm_start(int32_t n, const float* log_v1, const float* pred,
 fa_status fa_vec_axpby(int32_t n, float a, const float* x, float b,
                        const float* y, float* out, fa_stream_t stream);
 
+/*
+ * fa_plan_change -- how far the plan moved between two outer iterations,
+ * the convergence test of Algorithm 1's outer loop ("until S converges";
+ * reading: the L1 distance of the plans):
+ *     *l1_out = sum_ij | T_a,ij - T_b,ij |,
+ *     T = diag(exp(log_u)) K diag(exp(log_v)).
+ * K_a, K_b: device, n1 x ld in the context's storage type (padding columns
+ * ignored); log_u_* (n1), log_v_* (n2): device float32.  Each element's two
+ * plan values are formed in float32 and their differences summed in
+ * float64 in a fixed order.  l1_out: host; synchronises `stream`.
+ * FA_ERR_NUMERIC if the sum is not finite.
+ */
+fa_status fa_plan_change(fa_ctx* ctx, const void* K_a, const float* log_u_a,
+                         const float* log_v_a, const void* K_b, const float* log_u_b,
+                         const float* log_v_b, double* l1_out, fa_stream_t stream);
+
 /* ----------------------------------------------------------------------
  * fa_sinkhorn_step_static -- one fused Sinkhorn iteration that allocates
  * no device memory.  The paper has no counterpart: this entry serves

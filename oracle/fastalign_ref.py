@@ -68,6 +68,7 @@ __all__ = [
     "sinkhorn_scaling",
     "plan_log",
     "entropic_objective",
+    "plan_l1",
     "phase1",
     "fastalign",
     "topk",
@@ -268,6 +269,13 @@ def sinkhorn_scaling(K: np.ndarray, mu: np.ndarray, nu: np.ndarray, n_iter: int,
         S_col = v * (K.T @ u)
         errs.append(float(np.abs(S_col - nu).sum() + np.abs(u * (K @ v) - mu).sum()))
     return u, v, np.asarray(errs)
+
+
+def plan_l1(logS_a: np.ndarray, logS_b: np.ndarray) -> float:
+    """How far the plan moved between two outer iterations, the test of
+    Algorithm 1's outer loop ("until S converges"), read as the L1
+    distance sum_ij |S_a,ij - S_b,ij| of the plans given as log S."""
+    return float(np.abs(np.exp(logS_a) - np.exp(logS_b)).sum())
 
 
 def entropic_objective(S: np.ndarray, C: np.ndarray, eps: float) -> float:

@@ -90,6 +90,7 @@ SIGNATURES = {
     "fa_vec_axpby": (_i32, [_i32, ctypes.c_float, _p, ctypes.c_float, _p, _p, _p]),
     "fa_gnn_warm_start": (_i32, [_i32, _p, _p, ctypes.c_float, _p, _p]),
     "fa_sinkhorn_step_static": (_i32, [_p, _i32, _i32, _i32, _i64, _p, _p, _p, _p, _p, _p]),
+    "fa_plan_change": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _p]),
 }
 FA_GNN_FIN, FA_GNN_HIDDEN = 3, 64
 FA_GNN_NPARAMS = FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1
@@ -314,3 +315,11 @@ def fa_sinkhorn_step_static(K, dtype, n1, n2, ld, log_v, log_u, log_v_next, err,
                                          ptr(log_v), ptr(log_u), ptr(log_v_next), ptr(err),
                                          ptr(status), stream_ptr(stream)),
            "fa_sinkhorn_step_static")
+
+
+def fa_plan_change(ctx, K_a, log_u_a, log_v_a, K_b, log_u_b, log_v_b, stream=None) -> float:
+    out = _f64()
+    _check(lib().fa_plan_change(ctx, ptr(K_a), ptr(log_u_a), ptr(log_v_a), ptr(K_b),
+                                ptr(log_u_b), ptr(log_v_b), ctypes.byref(out),
+                                stream_ptr(stream)), "fa_plan_change")
+    return out.value

@@ -151,17 +151,74 @@ class Aligner:
     def last_sweep_ms(self):
         return L.fa_ctx_last_sweep_ms(self.ctx)
 
+    def plan_change(self, K, log_u, log_v, stream=None) -> float:
+        """sum_ij |T_ij - T'_ij| between the current plan and the plan held
+        as (K, log_u, log_v) (fa_plan_change)."""
+        return L.fa_plan_change(self.ctx, self.K, self.log_u, self.log_v, K, log_u, log_v,
+                                stream)
+
+    # -- checkpoint / resume of the outer loop
+    def save_checkpoint(self, path: str, t: int, extra: dict | None = None):
+        """Write the state an interrupted alignment resumes from: the Gibbs
+        kernel K, the log-scalings and the number t of outer iterations done.
+        C_node is not saved (fa_node_cost recomputes it deterministically)."""
+        torch.save({"format": "fastalign-checkpoint-1", "n1": self.n1, "n2": self.n2,
+                    "ld": self.ld, "dtype": self.params.dtype, "t": int(t),
+                    "K": self.K.cpu(), "log_u": self.log_u.cpu(), "log_v": self.log_v.cpu(),
+                    "extra": extra or {}}, path)
+
+    def load_checkpoint(self, path: str) -> int:
+        """Restore K and the log-scalings written by save_checkpoint; returns
+        the number of outer iterations they hold."""
+        ck = torch.load(path, map_location="cpu")
+        if ck.get("format") != "fastalign-checkpoint-1":
+            raise ValueError("not a checkpoint of this library")
+        if (ck["n1"], ck["n2"], ck["ld"], ck["dtype"]) != (self.n1, self.n2, self.ld,
+                                                          self.params.dtype):
+            raise ValueError("checkpoint shape or storage type does not match this aligner")
+        self.K.copy_(ck["K"])
+        self.log_u.copy_(ck["log_u"])
+        self.log_v.copy_(ck["log_v"])
+        return int(ck["t"])
+
     def align(self, X1, X2, anchors, n_outer: int, n_sink: int, tol: float = -1.0,
-              check_every: int = 1, warm=None):
-        """Algorithm 1 end to end; returns per-outer (iterations, error)."""
+              check_every: int = 1, warm=None, plan_tol: float | None = None,
+              checkpoint: str | None = None, resume: str | None = None):
+        """Algorithm 1 end to end; returns per-outer (iterations, error,
+        status[, plan change]).
+
+        plan_tol: stop before n_outer once an outer iteration moves the plan
+        by at most plan_tol in L1 (the outer loop's "until S converges").
+        checkpoint: write a checkpoint after every outer iteration.
+        resume: continue from a checkpoint (Phase 1 is recomputed)."""
         self.node_cost(X1, X2, anchors)
-        self.plan_init()
+        t0 = 0
+        if resume is not None:
+            t0 = self.load_checkpoint(resume)
+        else:
+            self.plan_init()
+        prev = None
+        if plan_tol is not None:
+            prev = (torch.empty_like(self.K), torch.empty_like(self.log_u),
+                    torch.empty_like(self.log_v))
+            for dst, src in zip(prev, (self.K, self.log_u, self.log_v)):
+                dst.copy_(src)
         hist = []
-        for _ in range(n_outer):
+        for t in range(t0, n_outer):
             self.align_iter()
             w = warm(self) if warm is not None else None
             it, err, st = self.sinkhorn(n_sink, tol, check_every, w)
-            hist.append((it, err, st))
+            if checkpoint is not None:
+                self.save_checkpoint(checkpoint, t + 1)
+            if prev is None:
+                hist.append((it, err, st))
+                continue
+            change = self.plan_change(*prev)
+            hist.append((it, err, st, change))
+            if change <= plan_tol:
+                break
+            for dst, src in zip(prev, (self.K, self.log_u, self.log_v)):
+                dst.copy_(src)
         return hist
 
     def close(self):

@@ -176,6 +176,7 @@ fa_status fa_ctx_destroy(fa_ctx* c) {
   dfree(c->logv_buf[0]); dfree(c->logv_buf[1]);
   dfree(c->intra1); dfree(c->intra2); dfree(c->anc_ptr); dfree(c->anc_col);
   dfree(c->err_part); dfree(c->ticket); dfree(c->err); dfree(c->status);
+  dfree(c->diff);
   for (auto& ev : c->sweep_events) cudaEventDestroy(ev);
   delete c;
   return FA_OK;
@@ -234,6 +235,7 @@ fa_status fa_ctx_create(const fa_graph* g1, const fa_graph* g2,
       (st = dalloc(&c->err_part, (size_t)((n2 + 255) / 256), acc)) != FA_OK ||
       (st = dalloc(&c->ticket, 1, acc)) != FA_OK ||
       (st = dalloc(&c->err, 1, acc)) != FA_OK ||
+      (st = dalloc(&c->diff, (size_t)kPlanDiffBlocks + 1, acc)) != FA_OK ||
       (st = dalloc(&c->status, 1, acc)) != FA_OK) {
     fa_ctx_destroy(c);
     return st;
@@ -542,6 +544,28 @@ fa_status fa_rank(fa_ctx* c, const void* K, const float* log_v, int32_t n_query,
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   FA_TRY(launch_exp_vec(c->n2, log_v, c->v_scale, s));
   return launch_rank(c->n2, c->ld, K, is_bf16(c), c->v_scale, n_query, rows, cols, rank_out, s);
+}
+
+// ------------------------------------------------------------ plan change
+fa_status fa_plan_change(fa_ctx* c, const void* K_a, const float* log_u_a,
+                         const float* log_v_a, const void* K_b, const float* log_u_b,
+                         const float* log_v_b, double* l1_out, fa_stream_t stream) {
+  if (!c || !K_a || !log_u_a || !log_v_a || !K_b || !log_u_b || !log_v_b || !l1_out) {
+    set_error("fa_plan_change: NULL argument");
+    return FA_ERR_ARG;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double* out = c->diff + kPlanDiffBlocks;
+  FA_TRY(launch_plan_l1diff(c->n1, c->n2, c->ld, is_bf16(c), K_a, log_u_a, log_v_a, K_b,
+                            log_u_b, log_v_b, c->diff, kPlanDiffBlocks, out, s));
+  FA_CUDA(cudaMemcpyAsync(&c->host_err, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FA_CUDA(cudaStreamSynchronize(s));
+  *l1_out = c->host_err;
+  if (!std::isfinite(*l1_out)) {
+    set_error("fa_plan_change: non-finite plan entries");
+    return FA_ERR_NUMERIC;
+  }
+  return FA_OK;
 }
 
 }  // extern "C"

@@ -156,6 +156,11 @@ fa_status launch_col_finalize(int n2, int64_t ld, int G, const float* colpart,
 fa_status launch_topk(int n1, int n2, int64_t ld, const void* K, bool bf16,
                       const float* log_v, int k, int32_t* idx, float* score,
                       cudaStream_t s);
+constexpr int kPlanDiffBlocks = 1024;
+fa_status launch_plan_l1diff(int n1, int n2, int64_t ld, bool bf16, const void* Ka,
+                             const float* lua, const float* lva, const void* Kb,
+                             const float* lub, const float* lvb, double* part, int nblocks,
+                             double* out, cudaStream_t s);
 fa_status launch_rank(int n2, int64_t ld, const void* K, bool bf16,
                       const float* log_v, int nq, const int32_t* rows,
                       const int32_t* cols, int32_t* rank, cudaStream_t s);
@@ -193,6 +198,7 @@ struct fa_ctx {
   double* err_part = nullptr;     // per finalize block
   unsigned* ticket = nullptr;
   double* err = nullptr;          // device scalar
+  double* diff = nullptr;         // plan-change block sums + result
   int* status = nullptr;          // device status word
   int64_t ws_bytes = 0;
   // timing

@@ -148,4 +148,65 @@ fa_status launch_rank(int n2, int64_t ld, const void* K, bool bf16,
   return FA_OK;
 }
 
+// ------------------------------------------------------------ plan change
+// sum_ij |T_a,ij - T_b,ij| with T = diag(exp(log_u)) K diag(exp(log_v)):
+// each element's two plan values in float32, their absolute difference
+// accumulated in float64.  Block b sums rows b, b + gridDim.x, ...; a
+// one-block kernel adds the block sums in index order (deterministic).
+constexpr int kDiffThreads = 256;
+
+template <typename TK>
+__global__ void __launch_bounds__(kDiffThreads) k_plan_l1diff(
+    int n1, int n2, int64_t ld, const TK* __restrict__ Ka, const float* __restrict__ lua,
+    const float* __restrict__ lva, const TK* __restrict__ Kb, const float* __restrict__ lub,
+    const float* __restrict__ lvb, double* __restrict__ part) {
+  __shared__ double red[kDiffThreads / 32];
+  double acc = 0.0;
+  for (int i = blockIdx.x; i < n1; i += gridDim.x) {
+    const float ua = expf(lua[i]), ub = expf(lub[i]);
+    const int64_t row = (int64_t)i * ld;
+    for (int j = threadIdx.x; j < n2; j += kDiffThreads) {
+      const float ta = ua * kval(Ka, row + j) * expf(lva[j]);
+      const float tb = ub * kval(Kb, row + j) * expf(lvb[j]);
+      acc += (double)fabsf(ta - tb);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kDiffThreads / 32; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_in_order(int n, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < n; ++b) t += part[b];
+    *out = t;
+  }
+}
+
+fa_status launch_plan_l1diff(int n1, int n2, int64_t ld, bool bf16, const void* Ka,
+                             const float* lua, const float* lva, const void* Kb,
+                             const float* lub, const float* lvb, double* part, int nblocks,
+                             double* out, cudaStream_t s) {
+  const int blocks = n1 < nblocks ? (n1 > 0 ? n1 : 1) : nblocks;
+  if (bf16)
+    k_plan_l1diff<__nv_bfloat16><<<blocks, kDiffThreads, 0, s>>>(
+        n1, n2, ld, static_cast<const __nv_bfloat16*>(Ka), lua, lva,
+        static_cast<const __nv_bfloat16*>(Kb), lub, lvb, part);
+  else
+    k_plan_l1diff<float><<<blocks, kDiffThreads, 0, s>>>(
+        n1, n2, ld, static_cast<const float*>(Ka), lua, lva, static_cast<const float*>(Kb),
+        lub, lvb, part);
+  FA_LAUNCHED("k_plan_l1diff");
+  k_sum_in_order<<<1, 32, 0, s>>>(blocks, part, out);
+  FA_LAUNCHED("k_sum_in_order");
+  return FA_OK;
+}
+
 }  // namespace fa

@@ -332,3 +332,23 @@ def test_planted_permutation_is_recovered():
     S = np.exp(out["logS"])
     r = R.rank_of(S, g.test_pairs[:, 0], g.test_pairs[:, 1])
     assert np.mean(r == 1) >= 0.98 and r.max() <= 3
+
+
+def test_plan_l1_definition():
+    # identical plans: 0; moving mass m between two entries: 2m; symmetric;
+    # matches the double loop; two probability plans are at most 2 apart
+    rng = np.random.default_rng(4)
+    S = rng.random((3, 4))
+    S /= S.sum()
+    assert R.plan_l1(np.log(S), np.log(S)) == 0.0
+    m = 0.05
+    S2 = S.copy()
+    S2[0, 0] -= m
+    S2[2, 3] += m
+    assert abs(R.plan_l1(np.log(S), np.log(S2)) - 2 * m) < 1e-15
+    assert R.plan_l1(np.log(S), np.log(S2)) == R.plan_l1(np.log(S2), np.log(S))
+    T = rng.random((3, 4))
+    T /= T.sum()
+    brute = sum(abs(S[i, j] - T[i, j]) for i in range(3) for j in range(4))
+    assert abs(R.plan_l1(np.log(S), np.log(T)) - brute) < 1e-15
+    assert R.plan_l1(np.log(S), np.log(T)) <= 2.0
