@@ -239,6 +239,42 @@ def test_sinkhorn_minimises_entropic_objective():
     assert R.entropic_objective(S, C, eps) <= f(res.x) + 1e-12
 
 
+def test_sinkhorn_kkt_additive_form_and_zero_duality_gap():
+    """Optimality of Eq. 1 under the marginal constraints, checked through
+    its dual rather than the iteration: (i) the stationarity condition
+    eps log S + C = a (+) b, an additive rank-2 form, leaves a zero
+    double-centring residual; (ii) the dual
+    D(a, b) = <a, nu> + <b, mu> - eps sum exp((a_j + b_i - C_ij) / eps)
+    equals the primal objective at the returned potentials; (iii) D is
+    concave and (a, b) maximises it, so no perturbation raises it.  Uneven
+    masses and n1 != n2, so a swapped index or a dropped log-marginal term
+    fails (ii)."""
+    rng = np.random.default_rng(11)
+    n1, n2 = 7, 5
+    C = rng.random((n1, n2))
+    mu = rng.random(n1)
+    mu /= mu.sum()
+    nu = rng.random(n2)
+    nu /= nu.sum()
+    eps = 0.3
+    a, b, errs, _ = R.sinkhorn_log(C, mu, nu, eps, 5000, tol=1e-14)
+    assert errs[-1] <= 1e-14
+    logS = R.plan_log(C, a, b, eps)
+    M = logS + C / eps
+    resid = M - M.mean(axis=1, keepdims=True) - M.mean(axis=0, keepdims=True) + M.mean()
+    assert np.abs(resid).max() <= 1e-12
+
+    def dual(a_, b_):
+        return float(a_ @ nu + b_ @ mu
+                     - eps * np.exp((a_[None, :] + b_[:, None] - C) / eps).sum())
+
+    primal = R.entropic_objective(np.exp(logS), C, eps)
+    assert abs(primal - dual(a, b)) <= 1e-12
+    d0 = dual(a, b)
+    for _ in range(200):
+        assert dual(a + rng.normal(0, 0.05, n2), b + rng.normal(0, 0.05, n1)) <= d0 + 1e-14
+
+
 def test_log_and_scaling_sinkhorn_agree():
     rng = np.random.default_rng(6)
     n1, n2 = 12, 9
