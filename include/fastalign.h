@@ -14,7 +14,8 @@
  *   (fa_graph, fa_ctx, fa_gnn) and frees it in the matching *_destroy.
  * - Calls that take a cudaStream_t enqueue their work on that stream and
  *   return without synchronising, except where they return a host scalar
- *   (fa_sinkhorn), which synchronises that stream only.
+ *   (fa_sinkhorn, fa_plan_change), which synchronises that stream only.
+ * - One fa_ctx serves one host thread and one stream at a time.
  * - Dense n1 x n2 matrices are row-major with a padded leading dimension
  *   ld = fa_ctx_ld(ctx) >= n2 (a multiple of 128 elements).  Padding columns
  *   of the Gibbs kernel K are written as 0 and must stay 0.

@@ -18,11 +18,43 @@ Typical use (Algorithm 1):
 from __future__ import annotations
 
 import dataclasses
+import os
 
 import numpy as np
 import torch
 
 from . import _lib as L
+
+
+CHECKPOINT_FORMAT = "fastalign-checkpoint-1"
+
+
+def write_checkpoint(path: str, state: dict) -> None:
+    """Write an outer-loop checkpoint atomically: the file is written under a
+    temporary name beside ``path`` and renamed over it, so an interruption
+    leaves the previous checkpoint intact."""
+    tmp = f"{path}.tmp.{os.getpid()}"
+    try:
+        torch.save({"format": CHECKPOINT_FORMAT, **state}, tmp)
+        os.replace(tmp, path)
+    finally:
+        if os.path.exists(tmp):
+            os.remove(tmp)
+
+
+def read_checkpoint(path: str, n1: int, n2: int, ld: int, dtype: str) -> dict:
+    """Read a checkpoint written by ``write_checkpoint`` and check that it
+    belongs to an aligner of the same shape and kernel storage type."""
+    ck = torch.load(path, map_location="cpu", weights_only=True)
+    if not isinstance(ck, dict) or ck.get("format") != CHECKPOINT_FORMAT:
+        raise ValueError("not a checkpoint of this library")
+    if (ck["n1"], ck["n2"], ck["ld"], ck["dtype"]) != (n1, n2, ld, dtype):
+        raise ValueError("checkpoint shape or storage type does not match this aligner")
+    want = torch.bfloat16 if dtype == "bf16" else torch.float32
+    if (tuple(ck["K"].shape) != (n1, ld) or ck["K"].dtype != want
+            or tuple(ck["log_u"].shape) != (n1,) or tuple(ck["log_v"].shape) != (n2,)):
+        raise ValueError("checkpoint arrays have the wrong shape or type")
+    return ck
 
 
 @dataclasses.dataclass
@@ -162,20 +194,15 @@ class Aligner:
         """Write the state an interrupted alignment resumes from: the Gibbs
         kernel K, the log-scalings and the number t of outer iterations done.
         C_node is not saved (fa_node_cost recomputes it deterministically)."""
-        torch.save({"format": "fastalign-checkpoint-1", "n1": self.n1, "n2": self.n2,
-                    "ld": self.ld, "dtype": self.params.dtype, "t": int(t),
-                    "K": self.K.cpu(), "log_u": self.log_u.cpu(), "log_v": self.log_v.cpu(),
-                    "extra": extra or {}}, path)
+        write_checkpoint(path, {"n1": self.n1, "n2": self.n2, "ld": self.ld,
+                                "dtype": self.params.dtype, "t": int(t),
+                                "K": self.K.cpu(), "log_u": self.log_u.cpu(),
+                                "log_v": self.log_v.cpu(), "extra": extra or {}})
 
     def load_checkpoint(self, path: str) -> int:
         """Restore K and the log-scalings written by save_checkpoint; returns
         the number of outer iterations they hold."""
-        ck = torch.load(path, map_location="cpu")
-        if ck.get("format") != "fastalign-checkpoint-1":
-            raise ValueError("not a checkpoint of this library")
-        if (ck["n1"], ck["n2"], ck["ld"], ck["dtype"]) != (self.n1, self.n2, self.ld,
-                                                          self.params.dtype):
-            raise ValueError("checkpoint shape or storage type does not match this aligner")
+        ck = read_checkpoint(path, self.n1, self.n2, self.ld, self.params.dtype)
         self.K.copy_(ck["K"])
         self.log_u.copy_(ck["log_u"])
         self.log_v.copy_(ck["log_v"])
