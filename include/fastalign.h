@@ -167,7 +167,12 @@ fa_status fa_align_iter(fa_ctx* ctx, void* K, float* log_u, float* log_v,
  * Out: log_u, log_v of the last completed iteration (a_t, b_t); *iters_out,
  *      *err_out (host, nullable) its count and error.
  * Returns FA_ERR_NOT_CONVERGED (state still valid) when tol >= 0 and the
- * cap was hit, FA_ERR_NUMERIC on NaN/Inf or an all-zero row or column.
+ * cap was hit, FA_ERR_NUMERIC on NaN/Inf or an all-zero row or column,
+ * FA_ERR_TIMEOUT when a bounded device-side wait gave up (results invalid;
+ * the context stays usable).  Both conditions are status bits kept in the
+ * context: a bit set by an earlier asynchronous call on it (fa_node_cost,
+ * fa_align_iter) is reported here too, and every bit is cleared once
+ * reported.  FA_ERR_TIMEOUT takes precedence.
  * Synchronises the stream when it reads the error back.
  * -------------------------------------------------------------------- */
 fa_status fa_sinkhorn(fa_ctx* ctx, const void* K, float* log_u, float* log_v,
@@ -316,6 +321,17 @@ fa_status fa_sinkhorn_step_static(const void* K, int32_t dtype, int32_t n1,
                                   int32_t n2, int64_t ld, const float* log_v,
                                   float* log_u, float* log_v_next, double* err,
                                   int32_t* status, fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * fa_ctx_selftest_wait -- failure-detection self-test (no counterpart in
+ * the paper).  Launches one kernel whose bounded wait, the one every
+ * mbarrier wait of the sweep uses, waits on a phase that nothing completes;
+ * it gives up after its limit (about 2 s), records the timeout bit in the
+ * context's status and returns normally.  Nothing is faulted.  The next
+ * fa_sinkhorn on the context then returns FA_ERR_TIMEOUT and clears the
+ * bit.  Asynchronous on `stream`.
+ * -------------------------------------------------------------------- */
+fa_status fa_ctx_selftest_wait(fa_ctx* ctx, fa_stream_t stream);
 
 /* Per-thread description of the last error. */
 const char* fa_last_error_string(void);

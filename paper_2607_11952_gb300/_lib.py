@@ -91,6 +91,7 @@ SIGNATURES = {
     "fa_gnn_warm_start": (_i32, [_i32, _p, _p, ctypes.c_float, _p, _p]),
     "fa_sinkhorn_step_static": (_i32, [_p, _i32, _i32, _i32, _i64, _p, _p, _p, _p, _p, _p]),
     "fa_plan_change": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _p]),
+    "fa_ctx_selftest_wait": (_i32, [_p, _p]),
 }
 FA_GNN_FIN, FA_GNN_HIDDEN = 3, 64
 FA_GNN_NPARAMS = FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1
@@ -216,6 +217,10 @@ def fa_sinkhorn(ctx, K, log_u, log_v, warm_log_v, max_iter, tol, check_every,
     if not (allow_not_converged and st == FA_ERR_NOT_CONVERGED):
         _check(st, "fa_sinkhorn")
     return it.value, err.value, st
+
+
+def fa_ctx_selftest_wait(ctx, stream=None) -> None:
+    _check(lib().fa_ctx_selftest_wait(ctx, stream_ptr(stream)), "fa_ctx_selftest_wait")
 
 
 def fa_topk(ctx, K, log_v, k, idx, score, stream=None) -> None:

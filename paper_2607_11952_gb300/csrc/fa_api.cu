@@ -459,7 +459,9 @@ fa_status fa_sinkhorn(fa_ctx* c, const void* K, float* log_u, float* log_v,
   SweepPlan sp = plan_sweep(n1, c->ld, bf16, c->G_sweep);
   if (warm_log_v)
     FA_CUDA(cudaMemcpyAsync(log_v, warm_log_v, n2 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  FA_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  // c->status is not cleared here: bits set by earlier asynchronous calls on
+  // this context (a bounded wait in the node-cost GEMM, a non-finite row in
+  // Pass B) are reported by this call, which clears them once read.
   const float mu = 1.0f / (float)n1, nu = 1.0f / (float)n2;
   float* bufs[3] = {log_v, c->logv_buf[0], c->logv_buf[1]};
   int cur = 0;
@@ -500,6 +502,7 @@ fa_status fa_sinkhorn(fa_ctx* c, const void* K, float* log_u, float* log_v,
   FA_CUDA(cudaStreamSynchronize(s));
   err = c->host_err;
   host_status = c->host_status;
+  if (host_status != 0) FA_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   if (c->timing) {
     double tot = 0.0;
     for (int t = 0; t < it; ++t) {
@@ -512,6 +515,11 @@ fa_status fa_sinkhorn(fa_ctx* c, const void* K, float* log_u, float* log_v,
   }
   if (iters_out) *iters_out = it;
   if (err_out) *err_out = err;
+  if (host_status & ST_TIMEOUT) {
+    set_error("fa_sinkhorn: a bounded device-side wait gave up (this call or an "
+              "earlier asynchronous call on the context); results are not valid");
+    return FA_ERR_TIMEOUT;
+  }
   if (host_status & ST_NUMERIC) {
     set_error("fa_sinkhorn: NaN/Inf or an all-zero row or column");
     return FA_ERR_NUMERIC;
@@ -544,6 +552,12 @@ fa_status fa_rank(fa_ctx* c, const void* K, const float* log_v, int32_t n_query,
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   FA_TRY(launch_exp_vec(c->n2, log_v, c->v_scale, s));
   return launch_rank(c->n2, c->ld, K, is_bf16(c), c->v_scale, n_query, rows, cols, rank_out, s);
+}
+
+// ------------------------------------------------------------ self-test
+fa_status fa_ctx_selftest_wait(fa_ctx* c, fa_stream_t stream) {
+  if (!c) { set_error("fa_ctx_selftest_wait: NULL ctx"); return FA_ERR_ARG; }
+  return launch_wait_selftest(c->status, reinterpret_cast<cudaStream_t>(stream));
 }
 
 // ------------------------------------------------------------ plan change

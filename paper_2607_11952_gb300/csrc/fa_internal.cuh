@@ -124,6 +124,7 @@ fa_status launch_exp_vec(int n, const float* x, float* y, cudaStream_t s);
 fa_status launch_fill(float* p, int64_t n, float v, cudaStream_t s);
 
 // Sinkhorn (Phase 3)
+fa_status launch_wait_selftest(int* status, cudaStream_t s);
 fa_status launch_plan_init(int n1, int n2, int64_t ld, void* K, bool bf16,
                            float* log_u, float* log_v, cudaStream_t s);
 fa_status launch_normalize_kernel(int n1, int n2, int64_t ld, const float* X,
