@@ -373,7 +373,8 @@ def _config(args, world):
                         f"{args.check_every}) + top-10",
             "n1": n1, "n2": n2, "outer": args.outer, "tol": args.tol,
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "l2": "inputs larger than L2 (K is 5 GB), no flush"}
+            "l2": f"inputs larger than L2 (K is {n1 * n2 * (4 if getattr(args, 'dtype', 'bf16') == 'f32' else 2) / 1e9:.1f} "
+                  f"GB), no flush"}
 
 
 def _synth_config(name):
