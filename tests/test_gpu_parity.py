@@ -218,6 +218,25 @@ def test_no_anchors_isolated_nodes_and_no_attributes():
     assert _rel(al.plan_f64(), np.exp(ref["logS"])) <= PLAN_TOL
 
 
+def test_edgeless_graph():
+    """G2 without a single edge: every CSR is empty, so RWR keeps only the
+    restart term, C2 and both right products vanish, the propagation of
+    C_node gives 0 and C_nbr is the clamp -log(delta) everywhere."""
+    rng = synth.rng_for(8)
+    n1, n2 = 60, 45
+    e1 = synth.erdos_renyi(n1, 3.0, rng)
+    e2 = np.zeros((0, 2), np.int64)
+    X1 = rng.standard_normal((n1, 8)).astype(np.float32)
+    X2 = rng.standard_normal((n2, 8)).astype(np.float32)
+    anchors = np.array([[0, 0], [5, 7], [9, 44]])
+    api = _api()
+    al = api.Aligner(api.Graph(n1, e1), api.Graph(n2, e2), api.Params())
+    assert al.g2.nnz == 0
+    al.align(X1, X2, anchors, n_outer=2, n_sink=20)
+    ref = R.fastalign(n1, n2, e1, e2, X1, X2, anchors, R.Params(), 2, 20)
+    assert _rel(al.plan_f64(), np.exp(ref["logS"])) <= PLAN_TOL
+
+
 def test_two_node_graphs():
     api = _api()
     e = np.array([[0, 1]])
