@@ -93,6 +93,19 @@ typedef struct fa_ctx fa_ctx;
  * -------------------------------------------------------------------- */
 fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
                          const int32_t* dst, fa_graph** out);
+
+/* ----------------------------------------------------------------------
+ * fa_graph_csr_host -- the host half of fa_build_graph (Alg. 1 L1), with
+ * no device work: the same CSR, returned in caller-owned host arrays.
+ * Call once with row_ptr = col = val_row = val_col = NULL to get *nnz_out;
+ * then with row_ptr of n + 1 entries and col, val_row (1/deg_i, Abar) and
+ * val_col (1/deg_k, Abar^T) of cap >= *nnz_out entries (FA_ERR_ARG
+ * otherwise).  Same argument checks and errors as fa_build_graph.
+ * -------------------------------------------------------------------- */
+fa_status fa_graph_csr_host(int32_t n, int64_t n_edges, const int32_t* src,
+                            const int32_t* dst, int64_t* nnz_out, int32_t* row_ptr,
+                            int32_t* col, float* val_row, float* val_col, int64_t cap);
+
 fa_status fa_graph_destroy(fa_graph* g);
 /* n and nnz (= 2 x unique undirected edges) of a built graph. */
 fa_status fa_graph_info(const fa_graph* g, int32_t* n, int64_t* nnz);
@@ -172,7 +185,8 @@ fa_status fa_align_iter(fa_ctx* ctx, void* K, float* log_u, float* log_v,
  * the context stays usable).  Both conditions are status bits kept in the
  * context: a bit set by an earlier asynchronous call on it (fa_node_cost,
  * fa_align_iter) is reported here too, and every bit is cleared once
- * reported.  FA_ERR_TIMEOUT takes precedence.
+ * reported.  FA_ERR_TIMEOUT takes precedence.  FA_ERR_UNSUPPORTED when no
+ * sweep shape fits a row of ld columns (ld > 196608; see fa_sweep_plan).
  * Synchronises the stream when it reads the error back.
  * -------------------------------------------------------------------- */
 fa_status fa_sinkhorn(fa_ctx* ctx, const void* K, float* log_u, float* log_v,
@@ -321,6 +335,19 @@ fa_status fa_sinkhorn_step_static(const void* K, int32_t dtype, int32_t n1,
                                   int32_t n2, int64_t ld, const float* log_v,
                                   float* log_u, float* log_v_next, double* err,
                                   int32_t* status, fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * fa_sweep_plan -- the launch shape fa_sinkhorn would use for the fused
+ * sweep (Alg. 1 L13-L16) on n1 rows of ld columns (ld a positive multiple
+ * of 128) in storage type dtype, from host logic only (no device query;
+ * the FA_SWEEP_* tuning variables apply).  out (host int32[8]) receives:
+ * cluster size Q, slab width W = ld / Q (elements), 16-byte vectors per
+ * thread per row S, rows per step R, ring stages NS, threads per CTA NT,
+ * kind (0 CTA-synchronous, 1 warp-specialised), and the cluster count G
+ * before the device's occupancy limit is applied.
+ * FA_ERR_UNSUPPORTED when no shape fits a row that wide.
+ * -------------------------------------------------------------------- */
+fa_status fa_sweep_plan(int32_t n1, int64_t ld, int32_t dtype, int32_t* out);
 
 /* ----------------------------------------------------------------------
  * fa_ctx_selftest_wait -- failure-detection self-test (no counterpart in

@@ -92,6 +92,9 @@ SIGNATURES = {
     "fa_sinkhorn_step_static": (_i32, [_p, _i32, _i32, _i32, _i64, _p, _p, _p, _p, _p, _p]),
     "fa_plan_change": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _p]),
     "fa_ctx_selftest_wait": (_i32, [_p, _p]),
+    "fa_graph_csr_host": (_i32, [_i32, _i64, _p, _p, ctypes.POINTER(_i64), _p, _p, _p, _p,
+                                 _i64]),
+    "fa_sweep_plan": (_i32, [_i32, _i64, _i32, _p]),
 }
 FA_GNN_FIN, FA_GNN_HIDDEN = 3, 64
 FA_GNN_NPARAMS = FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1
@@ -217,6 +220,37 @@ def fa_sinkhorn(ctx, K, log_u, log_v, warm_log_v, max_iter, tol, check_every,
     if not (allow_not_converged and st == FA_ERR_NOT_CONVERGED):
         _check(st, "fa_sinkhorn")
     return it.value, err.value, st
+
+
+def fa_graph_csr_host(n: int, src: np.ndarray, dst: np.ndarray):
+    """Host CSR of fa_build_graph: (row_ptr, col, val_row, val_col) as
+    NumPy arrays (int32, int32, float32, float32)."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = int(src.shape[0])
+    nnz = _i64()
+    _check(lib().fa_graph_csr_host(int(n), m, src.ctypes.data, dst.ctypes.data,
+                                   ctypes.byref(nnz), None, None, None, None, 0),
+           "fa_graph_csr_host")
+    k = int(nnz.value)
+    rp = np.empty(int(n) + 1, np.int32)
+    col = np.empty(max(k, 1), np.int32)
+    vr = np.empty(max(k, 1), np.float32)
+    vc = np.empty(max(k, 1), np.float32)
+    _check(lib().fa_graph_csr_host(int(n), m, src.ctypes.data, dst.ctypes.data,
+                                   ctypes.byref(nnz), rp.ctypes.data, col.ctypes.data,
+                                   vr.ctypes.data, vc.ctypes.data, max(k, 1)),
+           "fa_graph_csr_host")
+    return rp, col[:k], vr[:k], vc[:k]
+
+
+SWEEP_PLAN_FIELDS = ("Q", "W", "S", "R", "NS", "NT", "kind", "G")
+
+
+def fa_sweep_plan(n1: int, ld: int, dtype: int) -> dict:
+    out = (_i32 * 8)()
+    _check(lib().fa_sweep_plan(int(n1), int(ld), int(dtype), out), "fa_sweep_plan")
+    return dict(zip(SWEEP_PLAN_FIELDS, list(out)))
 
 
 def fa_ctx_selftest_wait(ctx, stream=None) -> None:

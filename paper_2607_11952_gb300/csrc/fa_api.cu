@@ -75,13 +75,24 @@ void fa_params_default(fa_params* p) {
 }
 
 // ------------------------------------------------------------ graphs
-fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
-                         const int32_t* dst, fa_graph** out) {
-  if (!out) { set_error("fa_build_graph: out is NULL"); return FA_ERR_ARG; }
-  *out = nullptr;
-  if (n < 1) { set_error("fa_build_graph: n=%d < 1", n); return FA_ERR_ARG; }
+}  // extern "C"
+
+namespace fa {
+
+// Host half of fa_build_graph (Alg. 1 L1): CSR of the symmetric adjacency
+// with columns ascending, values 1/deg_i (Abar) and 1/deg_k (Abar^T).
+struct HostCSR {
+  std::vector<int32_t> rp, col;
+  std::vector<float> vr, vc;
+  int32_t max_deg = 0;
+  int64_t nnz = 0;
+};
+
+static fa_status csr_from_edges(const char* who, int32_t n, int64_t n_edges,
+                                const int32_t* src, const int32_t* dst, HostCSR& h) {
+  if (n < 1) { set_error("%s: n=%d < 1", who, n); return FA_ERR_ARG; }
   if (n_edges < 0 || (n_edges > 0 && (!src || !dst))) {
-    set_error("fa_build_graph: bad edge arrays");
+    set_error("%s: bad edge arrays", who);
     return FA_ERR_ARG;
   }
   std::vector<int64_t> keys;
@@ -89,8 +100,7 @@ fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
   for (int64_t e = 0; e < n_edges; ++e) {
     const int32_t a = src[e], b = dst[e];
     if (a < 0 || a >= n || b < 0 || b >= n) {
-      set_error("fa_build_graph: edge %lld = (%d, %d) outside [0, %d)",
-                (long long)e, a, b, n);
+      set_error("%s: edge %lld = (%d, %d) outside [0, %d)", who, (long long)e, a, b, n);
       return FA_ERR_ARG;
     }
     if (a == b) continue;
@@ -105,30 +115,48 @@ fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
     deg[k % n]++;
   }
   const int64_t nnz = 2 * (int64_t)keys.size();
-  if (nnz > INT32_MAX) { set_error("fa_build_graph: too many edges"); return FA_ERR_UNSUPPORTED; }
-  std::vector<int32_t> rp(n + 1, 0), col(nnz), pos(n);
-  for (int i = 0; i < n; ++i) rp[i + 1] = rp[i] + deg[i];
-  for (int i = 0; i < n; ++i) pos[i] = rp[i];
+  if (nnz > INT32_MAX) { set_error("%s: too many edges", who); return FA_ERR_UNSUPPORTED; }
+  h.nnz = nnz;
+  h.rp.assign(n + 1, 0);
+  h.col.resize(nnz);
+  std::vector<int32_t> pos(n);
+  for (int i = 0; i < n; ++i) h.rp[i + 1] = h.rp[i] + deg[i];
+  for (int i = 0; i < n; ++i) pos[i] = h.rp[i];
   // keys are sorted by (u, v): every row receives its smaller neighbours
   // (as v) before its larger ones (as u), each group ascending.
   for (int64_t k : keys) {
     const int32_t u = (int32_t)(k / n), v = (int32_t)(k % n);
-    col[pos[u]++] = v;
-    col[pos[v]++] = u;
+    h.col[pos[u]++] = v;
+    h.col[pos[v]++] = u;
   }
-  std::vector<float> vr(nnz), vc(nnz);
-  int32_t maxd = 0;
+  h.vr.resize(nnz);
+  h.vc.resize(nnz);
+  h.max_deg = 0;
   for (int i = 0; i < n; ++i) {
-    maxd = std::max(maxd, deg[i]);
-    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
-      vr[e] = 1.0f / (float)deg[i];
-      vc[e] = 1.0f / (float)deg[col[e]];
+    h.max_deg = std::max(h.max_deg, deg[i]);
+    for (int32_t e = h.rp[i]; e < h.rp[i + 1]; ++e) {
+      h.vr[e] = 1.0f / (float)deg[i];
+      h.vc[e] = 1.0f / (float)deg[h.col[e]];
     }
   }
+  return FA_OK;
+}
+
+}  // namespace fa
+
+extern "C" {
+
+fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
+                         const int32_t* dst, fa_graph** out) {
+  if (!out) { set_error("fa_build_graph: out is NULL"); return FA_ERR_ARG; }
+  *out = nullptr;
+  HostCSR h;
+  FA_TRY(csr_from_edges("fa_build_graph", n, n_edges, src, dst, h));
+  const int64_t nnz = h.nnz;
   fa_graph* g = new fa_graph();
   g->d.n = n;
   g->d.nnz = nnz;
-  g->d.max_deg = maxd;
+  g->d.max_deg = h.max_deg;
   fa_status st;
   if ((st = dalloc(&g->d.row_ptr, n + 1)) != FA_OK ||
       (st = dalloc(&g->d.col, nnz)) != FA_OK ||
@@ -137,10 +165,10 @@ fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
     fa_graph_destroy(g);
     return st;
   }
-  cudaError_t e1 = cudaMemcpy(g->d.row_ptr, rp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
-  cudaError_t e2 = nnz ? cudaMemcpy(g->d.col, col.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice) : cudaSuccess;
-  cudaError_t e3 = nnz ? cudaMemcpy(g->d.val_row, vr.data(), nnz * sizeof(float), cudaMemcpyHostToDevice) : cudaSuccess;
-  cudaError_t e4 = nnz ? cudaMemcpy(g->d.val_col, vc.data(), nnz * sizeof(float), cudaMemcpyHostToDevice) : cudaSuccess;
+  cudaError_t e1 = cudaMemcpy(g->d.row_ptr, h.rp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+  cudaError_t e2 = nnz ? cudaMemcpy(g->d.col, h.col.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice) : cudaSuccess;
+  cudaError_t e3 = nnz ? cudaMemcpy(g->d.val_row, h.vr.data(), nnz * sizeof(float), cudaMemcpyHostToDevice) : cudaSuccess;
+  cudaError_t e4 = nnz ? cudaMemcpy(g->d.val_col, h.vc.data(), nnz * sizeof(float), cudaMemcpyHostToDevice) : cudaSuccess;
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
     set_error("fa_build_graph: upload failed: %s",
               cudaGetErrorString(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4));
@@ -148,6 +176,26 @@ fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
     return FA_ERR_CUDA;
   }
   *out = g;
+  return FA_OK;
+}
+
+fa_status fa_graph_csr_host(int32_t n, int64_t n_edges, const int32_t* src,
+                            const int32_t* dst, int64_t* nnz_out, int32_t* row_ptr,
+                            int32_t* col, float* val_row, float* val_col, int64_t cap) {
+  if (!nnz_out) { set_error("fa_graph_csr_host: nnz_out is NULL"); return FA_ERR_ARG; }
+  HostCSR h;
+  FA_TRY(csr_from_edges("fa_graph_csr_host", n, n_edges, src, dst, h));
+  *nnz_out = h.nnz;
+  if (!row_ptr && !col && !val_row && !val_col) return FA_OK;   // size query
+  if (!row_ptr || !col || !val_row || !val_col || cap < h.nnz) {
+    set_error("fa_graph_csr_host: need four arrays with room for %lld entries",
+              (long long)h.nnz);
+    return FA_ERR_ARG;
+  }
+  std::copy(h.rp.begin(), h.rp.end(), row_ptr);
+  std::copy(h.col.begin(), h.col.end(), col);
+  std::copy(h.vr.begin(), h.vr.end(), val_row);
+  std::copy(h.vc.begin(), h.vc.end(), val_col);
   return FA_OK;
 }
 
@@ -552,6 +600,25 @@ fa_status fa_rank(fa_ctx* c, const void* K, const float* log_v, int32_t n_query,
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   FA_TRY(launch_exp_vec(c->n2, log_v, c->v_scale, s));
   return launch_rank(c->n2, c->ld, K, is_bf16(c), c->v_scale, n_query, rows, cols, rank_out, s);
+}
+
+// ------------------------------------------------------------ sweep plan
+fa_status fa_sweep_plan(int32_t n1, int64_t ld, int32_t dtype, int32_t* out) {
+  if (!out) { set_error("fa_sweep_plan: out is NULL"); return FA_ERR_ARG; }
+  if (n1 < 1 || ld < 128 || ld % 128 != 0) {
+    set_error("fa_sweep_plan: n1=%d, ld=%lld (need n1 >= 1, ld a positive multiple of 128)",
+              n1, (long long)ld);
+    return FA_ERR_ARG;
+  }
+  if (dtype != FA_F32 && dtype != FA_BF16) { set_error("fa_sweep_plan: bad dtype %d", dtype); return FA_ERR_ARG; }
+  const SweepPlan sp = plan_sweep(n1, ld, dtype == FA_BF16, 1 << 20);
+  if (sp.Q < 1) {
+    set_error("fa_sweep_plan: no cluster shape fits a row of %lld elements", (long long)ld);
+    return FA_ERR_UNSUPPORTED;
+  }
+  const int32_t v[8] = {sp.Q, sp.W, sp.S, sp.R, sp.NS, sp.NT, sp.kind, sp.G};
+  std::copy(v, v + 8, out);
+  return FA_OK;
 }
 
 // ------------------------------------------------------------ self-test
