@@ -74,3 +74,30 @@ def test_chung_lu_tail_exponent(gamma):
     assert tail.size > 1000
     g_hat = 1.0 + tail.size / np.log(tail / 19.5).sum()
     assert abs(g_hat - gamma) < 0.2, g_hat
+
+
+def test_chung_lu_pair_noise_attributes_and_anchors():
+    """N11 noise for the Chung-Lu workloads (delete x% of G2's edges, add as
+    many non-edges: the edge count is kept), the relabelling carries every
+    kept edge that was not deleted, X2 = relabelled X1 + N(0, sigma^2), and
+    5% anchors."""
+    g = synth.config_pair("cl50k", n=4000)
+    e1 = {(int(u), int(v)) for u, v in g.edges1}
+    e2 = {(int(u), int(v)) for u, v in g.edges2}
+    assert len(e2) == len(e1)
+    mapped = {tuple(sorted((int(g.truth[u]), int(g.truth[v])))) for u, v in e1}
+    kept = len(mapped & e2)
+    assert kept == len(e1) - round(0.15 * len(e1))
+    diff = g.X2[g.truth] - g.X1
+    assert abs(float(diff.std()) - 0.1) < 0.005 and abs(float(diff.mean())) < 0.005
+    assert g.anchors.shape[0] == round(0.05 * 4000)
+    assert len({int(i) for i, _ in g.anchors} & {int(i) for i, _ in g.test_pairs}) == 0
+
+
+def test_seeded_generators_are_reproducible():
+    a = synth.config_pair("cl10k", n=1500)
+    b = synth.config_pair("cl10k", n=1500)
+    for f in ("edges1", "edges2", "X1", "X2", "anchors", "truth", "test_pairs"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+    c = synth.config_pair("cl10k", n=1500, seed=99)
+    assert not np.array_equal(a.edges1, c.edges1)
