@@ -16,11 +16,8 @@ from __future__ import annotations
 
 import argparse
 import json
-import os
-import sys
 import time
 
-import numpy as np
 import torch
 
 from . import api, gnn, synth
