@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(256) k_sddmm(
   }
 }
 
-fa_status launch_sddmm(const DevGraph& g, int L, int64_t ldr, const float* R,
+// The dot products run over all ldr columns of R: the padding columns past
+// the L anchors stay 0 through the RWR, so they add nothing.
+fa_status launch_sddmm(const DevGraph& g, int /*L*/, int64_t ldr, const float* R,
                        bool weight_by_col, float* out, cudaStream_t s) {
   if (g.nnz == 0) return FA_OK;
   int64_t threads = (int64_t)g.n * 32;
