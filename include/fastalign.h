@@ -51,7 +51,7 @@ typedef enum {
 
 typedef enum { FA_F32 = 0, FA_BF16 = 1 } fa_dtype;
 
-/* GEMM engine for the node-similarity cost (Alg. 1 L4). */
+/* GEMM engine for the node-similarity cost (Algorithm 1, node cost). */
 typedef enum {
   FA_GEMM_AUTO = 0,      /* tcgen05: bf16 operands for FA_BF16, 3xTF32 split for FA_F32 */
   FA_GEMM_TCGEN05 = 1,   /* same as AUTO */
@@ -62,11 +62,11 @@ typedef enum {
 typedef struct {
   int32_t dtype;              /* fa_dtype: storage type of the Gibbs kernel K */
   float eps;                  /* entropic regulariser (Eq. 1, Eq. 3) */
-  float eps_anc;              /* eps inside C_anc = -log(eps_anc + OneHot(L)) (Alg. 1 L6) */
-  float alpha;                /* node-cost mix (Alg. 1 L4) */
-  float beta;                 /* RWR restart probability (Alg. 1 L3) */
-  int32_t k_rwr;              /* RWR iterations (Alg. 1 L3) */
-  int32_t k_prop;             /* C_node propagation steps A1bar C A2bar^T (Alg. 1 L5) */
+  float eps_anc;              /* eps inside C_anc = -log(eps_anc + OneHot(L)) (Algorithm 1, anchor cost) */
+  float alpha;                /* node-cost mix (Algorithm 1, node cost) */
+  float beta;                 /* RWR restart probability (Algorithm 1, RWR) */
+  int32_t k_rwr;              /* RWR iterations (Algorithm 1, RWR) */
+  int32_t k_prop;             /* C_node propagation steps A1bar C A2bar^T (Algorithm 1) */
   float lam_e, lam_n, lam_a;  /* cost weights (Eq. 2) */
   float lam_p;                /* proximal weight: C_eff = C - lam_p log T_prev */
   float delta;                /* clamp inside -log(max(., delta)) of C_nbr */
@@ -83,7 +83,7 @@ typedef struct fa_graph fa_graph;
 typedef struct fa_ctx fa_ctx;
 
 /* ----------------------------------------------------------------------
- * fa_build_graph -- Alg. 1 L1 (row normalisation, Section 3.3 sparse form).
+ * fa_build_graph -- Algorithm 1, row normalisation (Section 3.3 sparse form).
  * n: node count (>= 1).  src, dst: host int32 arrays of n_edges undirected
  * edges; self-loops and duplicates are dropped, node ids must lie in
  * [0, n) (FA_ERR_ARG otherwise).  Builds on the current device the CSR of
@@ -95,7 +95,7 @@ fa_status fa_build_graph(int32_t n, int64_t n_edges, const int32_t* src,
                          const int32_t* dst, fa_graph** out);
 
 /* ----------------------------------------------------------------------
- * fa_graph_csr_host -- the host half of fa_build_graph (Alg. 1 L1), with
+ * fa_graph_csr_host -- the host half of fa_build_graph (Algorithm 1, row normalisation), with
  * no device work: the same CSR, returned in caller-owned host arrays.
  * Call once with row_ptr = col = val_row = val_col = NULL to get *nnz_out;
  * then with row_ptr of n + 1 entries and col, val_row (1/deg_i, Abar) and
@@ -125,11 +125,11 @@ int64_t fa_ctx_ld(const fa_ctx* ctx);
 int64_t fa_ctx_workspace_bytes(const fa_ctx* ctx);
 
 /* ----------------------------------------------------------------------
- * fa_node_cost -- Phase 1 of Algorithm 1 (L2-L7):
- *   R_g  <- k_rwr steps of (1-beta) Abar_g R_g + beta R_g^(0)     (L2-L3)
- *   C_node = alpha exp(-R1 R2^T) + (1-alpha) exp(-X1h X2h^T)      (L4)
- *   C_node <- k_prop steps of A1bar C_node A2bar^T                 (L5)
- *   C1 = (R1 R1^T) .* A1bar,  C2 = (R2 R2^T) .* A2bar^T  (SDDMM)    (L7)
+ * fa_node_cost -- Phase 1 of Algorithm 1:
+ *   R_g  <- k_rwr steps of (1-beta) Abar_g R_g + beta R_g^(0)     (RWR)
+ *   C_node = alpha exp(-R1 R2^T) + (1-alpha) exp(-X1h X2h^T)      (node cost)
+ *   C_node <- k_prop steps of A1bar C_node A2bar^T                 (propagation)
+ *   C1 = (R1 R1^T) .* A1bar,  C2 = (R2 R2^T) .* A2bar^T  (SDDMM)    (intra-graph costs)
  * X1 (n1 x d), X2 (n2 x d): device float32 row-major attributes (d >= 1,
  * may be NULL with d = 0 to drop the attribute term's variation: exp(0)).
  * anchors: host int32 [n_anchor][2] pairs (i, j); 0 <= n_anchor.
@@ -151,13 +151,13 @@ fa_status fa_plan_init(fa_ctx* ctx, void* K, float* log_u, float* log_v,
                        fa_stream_t stream);
 
 /* ----------------------------------------------------------------------
- * fa_align_iter -- Phase 2 of one outer iteration (Alg. 1 L10-L12) and
+ * fa_align_iter -- Phase 2 of one outer iteration (Algorithm 1) and
  * the Gibbs kernel of the proximal step:
  *   W   = P1 T_prev           P1 in {C1, A1bar^T}        (left SpMMs)
  *   Z   = W P2^T              P2 in {C2, A2bar^T}         (right SpMMs)
  *   C   = C_node + lam_e Z_e - lam_n log max(Z_n, delta) + lam_a C_anc
  *   log K_new = -C/eps + (lam_p/eps) log T_prev,  row-max stabilised
- * then the first Sinkhorn column update a_1 (Eq. 3, Alg. 1 L14) from the
+ * then the first Sinkhorn column update a_1 (Eq. 3, Algorithm 1 Phase 3) from the
  * row-stabilised start b0.
  * In:  K (T_prev's kernel), log_u, log_v, C_node (from fa_node_cost).
  * Out: K overwritten in place by the new row-stabilised kernel (row max 1),
@@ -167,7 +167,7 @@ fa_status fa_align_iter(fa_ctx* ctx, void* K, float* log_u, float* log_v,
                         const float* C_node, fa_stream_t stream);
 
 /* ----------------------------------------------------------------------
- * fa_sinkhorn -- Phase 3 (Alg. 1 L13-L16, Eq. 3) on a fixed kernel K.
+ * fa_sinkhorn -- Phase 3 of Algorithm 1 (Eq. 3) on a fixed kernel K.
  * One fused sweep per iteration reads K once: the row update
  * u_i = mu_i / sum_j K_ij v_j (b update) and, in the same pass, the column
  * sums sum_i K_ij u_i for the next column update (a update).  The L1
@@ -338,7 +338,7 @@ fa_status fa_sinkhorn_step_static(const void* K, int32_t dtype, int32_t n1,
 
 /* ----------------------------------------------------------------------
  * fa_sweep_plan -- the launch shape fa_sinkhorn would use for the fused
- * sweep (Alg. 1 L13-L16) on n1 rows of ld columns (ld a positive multiple
+ * sweep (Algorithm 1, Phase 3) on n1 rows of ld columns (ld a positive multiple
  * of 128) in storage type dtype, from host logic only (no device query;
  * the FA_SWEEP_* tuning variables apply).  out (host int32[8]) receives:
  * cluster size Q, slab width W = ld / Q (elements), 16-byte vectors per

@@ -10,8 +10,10 @@ which holds none of the method's arithmetic.
 Everything is float64 NumPy / SciPy.sparse, written in the order and
 notation of the paper:
 
-* Algorithm 1 (linear-algebraic view of OT-based alignment), Phase 1 lines
-  L1-L8, Phase 2 lines L10-L12, Phase 3 lines L13-L17.
+* Algorithm 1 (linear-algebraic view of OT-based alignment): Phase 1
+  (normalisation, RWR, node, anchor and intra-graph costs, initial plan),
+  Phase 2 (edge and neighbourhood costs, cost assembly), Phase 3 (Sinkhorn)
+  and the alignment output.
 * Eq. 1 (entropic OT objective), Eq. 2 (cost decomposition), Eq. 3 (log-domain
   Sinkhorn dual updates), Eq. 4 (plan recovery).
 * Section 4.1.1 (Hits@K, MRR).
@@ -35,7 +37,7 @@ R-b0     The initial row potential of each solve is the row stabiliser
          b0_i = -eps max_j(-C_eff_ij / eps), which makes every row of the
          initial Gibbs kernel peak at 1.  The paper does not state b0.
 R-order  One Sinkhorn iteration is the a update then the b update
-         (Algorithm 1 L14-L15); the marginal error is measured after the b
+         (Algorithm 1, Phase 3); the marginal error is measured after the b
          update (rows are then exact): err = |S^T 1 - nu|_1 + |S 1 - mu|_1.
 R-clamp  C_nbr = -log(max(Z, delta)) so isolated nodes and underflowed
          entries stay finite.
@@ -83,15 +85,15 @@ class Params:
     """Hyper-parameters of Algorithm 1.  The paper names them but gives no
     values; these defaults were fixed once on the 1k Barabasi-Albert pair."""
     eps: float = 0.05          # entropic regulariser (Eq. 1)
-    eps_anc: float = 0.05      # the eps inside C_anc (Alg. 1 L6)
-    alpha: float = 0.5         # node-cost mix (Alg. 1 L4)
-    beta: float = 0.15         # restart probability of the RWR (Alg. 1 L3)
-    k_rwr: int = 10            # RWR iterations (Alg. 1 L3)
-    k_prop: int = 1            # C_node propagation steps (Alg. 1 L5)
+    eps_anc: float = 0.05      # the eps inside C_anc (Algorithm 1, anchor cost)
+    alpha: float = 0.5         # node-cost mix (Algorithm 1, node cost)
+    beta: float = 0.15         # restart probability of the RWR (Algorithm 1)
+    k_rwr: int = 10            # RWR iterations (Algorithm 1)
+    k_prop: int = 1            # C_node propagation steps (Algorithm 1)
     lam_e: float = 1.0         # edge-consistency weight (Eq. 2)
     lam_n: float = 0.05        # neighbourhood-consistency weight (Eq. 2)
     lam_a: float = 0.05        # anchor weight (Eq. 2)
-    lam_p: float = 0.05        # proximal weight (Section 3.1, L12 text)
+    lam_p: float = 0.05        # proximal weight (Section 3.1; the cost assembly of Algorithm 1)
     delta: float = 1e-30       # clamp inside -log(.) of C_nbr
     normalize_features: bool = True
 
@@ -99,7 +101,7 @@ class Params:
 # ---------------------------------------------------------------- Phase 1
 
 def row_normalized(n: int, edges: np.ndarray) -> sp.csr_matrix:
-    """Alg. 1 L1: symmetric 0/1 adjacency (duplicates and self-loops
+    """Algorithm 1, row normalisation: symmetric 0/1 adjacency (duplicates and self-loops
     dropped) divided by its degree, Abar = D^{-1} A; degree-0 rows stay 0."""
     e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
     e = e[e[:, 0] != e[:, 1]]
@@ -115,7 +117,7 @@ def row_normalized(n: int, edges: np.ndarray) -> sp.csr_matrix:
 
 
 def one_hot_anchors(n1: int, n2: int, anchors: np.ndarray):
-    """Alg. 1 L2: R1^(0)[i_l, l] = 1 and R2^(0)[j_l, l] = 1 for anchor l."""
+    """Algorithm 1, anchor encoding: R1^(0)[i_l, l] = 1 and R2^(0)[j_l, l] = 1 for anchor l."""
     L = anchors.shape[0]
     R1 = np.zeros((n1, L))
     R2 = np.zeros((n2, L))
@@ -126,7 +128,7 @@ def one_hot_anchors(n1: int, n2: int, anchors: np.ndarray):
 
 
 def rwr(Abar: sp.csr_matrix, R0: np.ndarray, beta: float, k: int) -> np.ndarray:
-    """Alg. 1 L3: k iterations of R <- (1-beta) Abar R + beta R^(0),
+    """Algorithm 1, RWR: k iterations of R <- (1-beta) Abar R + beta R^(0),
     starting from R = R^(0)."""
     R = R0.copy()
     for _ in range(k):
@@ -142,12 +144,12 @@ def normalize_features(X: np.ndarray) -> np.ndarray:
 
 
 def initial_node_cost(R1, R2, X1h, X2h, alpha: float) -> np.ndarray:
-    """Alg. 1 L4: C_node = alpha exp(-R1 R2^T) + (1-alpha) exp(-X1 X2^T)."""
+    """Algorithm 1, node cost: C_node = alpha exp(-R1 R2^T) + (1-alpha) exp(-X1 X2^T)."""
     return alpha * np.exp(-(R1 @ R2.T)) + (1.0 - alpha) * np.exp(-(X1h @ X2h.T))
 
 
 def propagate_node_cost(A1bar, A2bar, C: np.ndarray, k: int) -> np.ndarray:
-    """Alg. 1 L5 with reading R-prop: k times C <- A1bar C A2bar^T,
+    """Algorithm 1, propagation, with reading R-prop: k times C <- A1bar C A2bar^T,
     evaluated as two sparse-dense products (Section 3.3)."""
     for _ in range(k):
         C = np.asarray(A1bar @ C)                 # left SpMM
@@ -156,7 +158,7 @@ def propagate_node_cost(A1bar, A2bar, C: np.ndarray, k: int) -> np.ndarray:
 
 
 def anchor_cost(n1: int, n2: int, anchors: np.ndarray, eps_anc: float) -> np.ndarray:
-    """Alg. 1 L6 (reading R-anc): C_anc = -log(eps_anc + OneHot(L))."""
+    """Algorithm 1, anchor cost (reading R-anc): C_anc = -log(eps_anc + OneHot(L))."""
     H = np.zeros((n1, n2))
     for i, j in np.asarray(anchors, dtype=np.int64):
         H[i, j] = 1.0
@@ -164,7 +166,7 @@ def anchor_cost(n1: int, n2: int, anchors: np.ndarray, eps_anc: float) -> np.nda
 
 
 def intra_costs(R1, R2, A1bar: sp.csr_matrix, A2bar: sp.csr_matrix):
-    """Alg. 1 L7: C1 = (R1 R1^T) .* A1bar and C2 = (R2 R2^T) .* A2bar^T,
+    """Algorithm 1, intra-graph costs: C1 = (R1 R1^T) .* A1bar and C2 = (R2 R2^T) .* A2bar^T,
     evaluated dense-then-masked (the plain definition, not an SDDMM)."""
     M1 = A1bar.toarray()
     M2 = A2bar.T.toarray()
@@ -176,19 +178,19 @@ def intra_costs(R1, R2, A1bar: sp.csr_matrix, A2bar: sp.csr_matrix):
 # ---------------------------------------------------------------- Phase 2
 
 def edge_cost(C1: sp.csr_matrix, S: np.ndarray, C2: sp.csr_matrix) -> np.ndarray:
-    """Alg. 1 L10: C_edge = C1 S C2^T (two SpMMs)."""
+    """Algorithm 1, edge cost: C_edge = C1 S C2^T (two SpMMs)."""
     return np.asarray((C2 @ np.asarray(C1 @ S).T).T)
 
 
 def nbr_cost(A1bar: sp.csr_matrix, S: np.ndarray, A2bar: sp.csr_matrix,
              delta: float) -> np.ndarray:
-    """Alg. 1 L11 (reading R-clamp): C_nbr = -log(max(A1bar^T S A2bar, delta))."""
+    """Algorithm 1, neighbourhood cost (reading R-clamp): C_nbr = -log(max(A1bar^T S A2bar, delta))."""
     Z = np.asarray((A2bar.T @ np.asarray(A1bar.T @ S).T).T)
     return -np.log(np.maximum(Z, delta))
 
 
 def total_cost(C_node, C_edge, C_nbr, C_anc, p: Params) -> np.ndarray:
-    """Alg. 1 L12 / Eq. 2: C = C_node + lam_e C_edge + lam_n C_nbr + lam_a C_anc."""
+    """Algorithm 1, cost assembly / Eq. 2: C = C_node + lam_e C_edge + lam_n C_nbr + lam_a C_anc."""
     return C_node + p.lam_e * C_edge + p.lam_n * C_nbr + p.lam_a * C_anc
 
 
@@ -294,14 +296,14 @@ class Phase1:
     R1: np.ndarray
     R2: np.ndarray
     C_node: np.ndarray          # after propagation
-    C_node0: np.ndarray         # before propagation (Alg. 1 L4)
+    C_node0: np.ndarray         # before propagation (node cost of Algorithm 1)
     C_anc: np.ndarray
     C1: sp.csr_matrix
     C2: sp.csr_matrix
 
 
 def phase1(n1, n2, edges1, edges2, X1, X2, anchors, p: Params) -> Phase1:
-    """Alg. 1 L1-L7: the S-independent quantities."""
+    """Phase 1 of Algorithm 1: the S-independent quantities."""
     A1 = row_normalized(n1, edges1)
     A2 = row_normalized(n2, edges2)
     R10, R20 = one_hot_anchors(n1, n2, anchors)
@@ -319,7 +321,7 @@ def phase1(n1, n2, edges1, edges2, X1, X2, anchors, p: Params) -> Phase1:
 
 
 def outer_step(ph: Phase1, logS_prev: np.ndarray, p: Params):
-    """Alg. 1 L10-L12 plus reading R-prox: the effective cost of one outer
+    """Phase 2 of Algorithm 1 plus reading R-prox: the effective cost of one outer
     iteration, C_eff = C(S_prev) - lam_p log S_prev."""
     S = np.exp(logS_prev)
     Ce = edge_cost(ph.C1, S, ph.C2)

@@ -2,20 +2,20 @@
 
 TEST INFRASTRUCTURE ONLY (like ``fastalign_ref``): used by the full-size
 parity tests, which cannot hold the dense n1 x n2 matrices of the plain
-oracle in host memory.  Each quantity of Algorithm 1 L1-L12 is the plain
+oracle in host memory.  Each quantity of Phases 1-2 of Algorithm 1 is the plain
 definition evaluated at the requested rows i of the n1 x n2 matrices:
 
-* Alg. 1 L1-L3: Abar = D^{-1} A and the RWR encodings R1, R2 (whole, they
+* Row normalisation and RWR: Abar = D^{-1} A and the RWR encodings R1, R2 (whole, they
   are n x |L|), from ``fastalign_ref``.
-* Alg. 1 L4: C_node^(0)[k, :] = alpha exp(-R1[k] R2^T) + (1-alpha)
+* Node cost: C_node^(0)[k, :] = alpha exp(-R1[k] R2^T) + (1-alpha)
   exp(-X1h[k] X2h^T) for the rows k the propagation needs.
-* Alg. 1 L5 (reading R-prop): row i of A1bar C A2bar^T is
+* Propagation (reading R-prop): row i of A1bar C A2bar^T is
   A2bar (A1bar[i, :] C)^T, needing the rows of C at the neighbours of i.
-* Alg. 1 L10-L11 at the first outer iteration, whose plan is the
+* Edge and neighbourhood products at the first outer iteration, whose plan is the
   independent coupling S0 = mu nu^T (reading R-init), a rank-one matrix:
   C1 S0 C2^T = (C1 mu)(C2 nu)^T and A1bar^T S0 A2bar = (A1bar^T mu)(A2bar^T nu)^T
   (associativity of the matrix products in the definitions).
-* Alg. 1 L6, L12 (readings R-anc, R-clamp) and the proximal step (R-prox):
+* Anchor cost and cost assembly (readings R-anc, R-clamp) and the proximal step (R-prox):
   C_eff = C - lam_p log S0, x = -C_eff / eps, and the row-stabilised kernel
   K[i, :] = exp(x[i, :] - max_j x[i, j]) (reading R-b0), which is what the
   library stores.
@@ -34,13 +34,13 @@ from . import fastalign_ref as R
 
 
 def _node_cost_rows(ks, R1, R2, X1h, X2h, alpha):
-    """Alg. 1 L4 at rows ``ks``."""
+    """Node cost (Algorithm 1) at rows ``ks``."""
     ks = np.asarray(ks, dtype=np.int64)
     return alpha * np.exp(-(R1[ks] @ R2.T)) + (1.0 - alpha) * np.exp(-(X1h[ks] @ X2h.T))
 
 
 def _propagated_rows(rows, A1, A2, R1, R2, X1h, X2h, alpha, k_prop):
-    """Alg. 1 L5 (R-prop), k_prop times, at ``rows``: each level needs the
+    """Propagation (Algorithm 1, R-prop), k_prop times, at ``rows``: each level needs the
     rows of the previous level at the neighbours of its own rows."""
     levels = [np.unique(np.asarray(rows, dtype=np.int64))]
     for _ in range(k_prop):
@@ -65,7 +65,7 @@ def _propagated_rows(rows, A1, A2, R1, R2, X1h, X2h, alpha, k_prop):
 
 
 def _c1_times_vector(A1: sp.csr_matrix, R1: np.ndarray, m: np.ndarray, rows):
-    """(C1 m)[i] for C1 = (R1 R1^T) .* A1bar (Alg. 1 L7), at ``rows``."""
+    """(C1 m)[i] for C1 = (R1 R1^T) .* A1bar (Algorithm 1, intra-graph costs), at ``rows``."""
     out = np.zeros(len(rows))
     for t, i in enumerate(rows):
         lo, hi = A1.indptr[i], A1.indptr[i + 1]
@@ -75,7 +75,7 @@ def _c1_times_vector(A1: sp.csr_matrix, R1: np.ndarray, m: np.ndarray, rows):
 
 
 def _c2_times_vector(A2: sp.csr_matrix, R2: np.ndarray, v: np.ndarray, chunk=20000):
-    """(C2 v)[j] for C2 = (R2 R2^T) .* A2bar^T (Alg. 1 L7), for every j:
+    """(C2 v)[j] for C2 = (R2 R2^T) .* A2bar^T (Algorithm 1, intra-graph costs), for every j:
     sum over the stored entries (l, j) of A2bar of A2bar[l, j] <R2[j], R2[l]> v[l]."""
     Acoo = A2.tocoo()
     out = np.zeros(A2.shape[0])
@@ -111,7 +111,7 @@ class Phase1Rows:
 
 
 def prepare(n1, n2, edges1, edges2, X1, X2, anchors, p: R.Params) -> Phase1Rows:
-    """Alg. 1 L1-L3 and the attribute normalisation (R-feat)."""
+    """Row normalisation, RWR and the attribute normalisation (R-feat)."""
     A1 = R.row_normalized(n1, edges1)
     A2 = R.row_normalized(n2, edges2)
     R10, R20 = R.one_hot_anchors(n1, n2, anchors)
@@ -136,7 +136,7 @@ def first_kernel_rows_from(st: Phase1Rows, anchors, p: R.Params, rows,
                            operands: str = "f64"):
     """As ``first_kernel_rows`` from prepared quantities.  operands="bf16"
     is the BF16 form of the method: the two node-similarity products of
-    Alg. 1 L4 take their operands (R1, R2, X1h, X2h) rounded to bfloat16,
+    the node cost of Algorithm 1 take their operands (R1, R2, X1h, X2h) rounded to bfloat16,
     with exact products and sums; everything else stays float64."""
     rows = [int(i) for i in rows]
     n1, n2, A1, A2 = st.n1, st.n2, st.A1, st.A2

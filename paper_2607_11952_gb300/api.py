@@ -8,11 +8,11 @@ Typical use (Algorithm 1):
 
     g1, g2 = Graph(n1, edges1), Graph(n2, edges2)
     al = Aligner(g1, g2, Params(dtype="bf16"))
-    al.node_cost(X1, X2, anchors)          # Phase 1 (L1-L7)
+    al.node_cost(X1, X2, anchors)          # Phase 1 of Algorithm 1
     al.plan_init()                         # S0 = mu nu^T
     for t in range(T):                     # outer iterations
-        al.align_iter()                    # Phase 2 (L10-L12) + Gibbs kernel
-        al.sinkhorn(max_iter=50)           # Phase 3 (L13-L16, Eq. 3)
+        al.align_iter()                    # Phase 2 + Gibbs kernel
+        al.sinkhorn(max_iter=50)           # Phase 3 (Eq. 3)
     idx, score = al.topk(10)               # read-out (Section 4.1.1)
 """
 from __future__ import annotations

@@ -79,7 +79,7 @@ void fa_params_default(fa_params* p) {
 
 namespace fa {
 
-// Host half of fa_build_graph (Alg. 1 L1): CSR of the symmetric adjacency
+// Host half of fa_build_graph (Algorithm 1, row normalisation): CSR of the symmetric adjacency
 // with columns ascending, values 1/deg_i (Abar) and 1/deg_k (Abar^T).
 struct HostCSR {
   std::vector<int32_t> rp, col;
@@ -394,7 +394,7 @@ fa_status fa_node_cost(fa_ctx* c, const float* X1, const float* X2, int32_t d,
     freeall();
     return FA_ERR_CUDA;
   }
-  // Alg. 1 L2-L3: R <- (1-beta) Abar R + beta R^(0), k_rwr times
+  // Algorithm 1, RWR: R <- (1-beta) Abar R + beta R^(0), k_rwr times
   const float beta = c->p.beta;
   FA_STEP(launch_onehot(n1, L, ldr, da1, R1a, s));
   FA_STEP(launch_onehot(n2, L, ldr, da2, R2a, s));
@@ -406,7 +406,7 @@ fa_status fa_node_cost(fa_ctx* c, const float* X1, const float* X2, int32_t d,
     FA_STEP(launch_add_onehot(L, ldr, da2, beta, R2b, s));
     std::swap(R2a, R2b);
   }
-  // Alg. 1 L7: SDDMM for C1 (1/deg i) and C2 (1/deg l)
+  // Algorithm 1, intra-graph costs: SDDMM for C1 (1/deg i) and C2 (1/deg l)
   FA_STEP(launch_sddmm(c->g1->d, L, ldr, R1a, false, c->intra1, s));
   FA_STEP(launch_sddmm(c->g2->d, L, ldr, R2a, true, c->intra2, s));
   // attributes
@@ -417,7 +417,7 @@ fa_status fa_node_cost(fa_ctx* c, const float* X1, const float* X2, int32_t d,
     FA_STEP(launch_fill(X1h, (int64_t)n1 * ldx, 0.f, s));
     FA_STEP(launch_fill(X2h, (int64_t)n2 * ldx, 0.f, s));
   }
-  // Alg. 1 L4: the node-similarity GEMMs with the exp epilogue
+  // Algorithm 1, node cost: the node-similarity GEMMs with the exp epilogue
   const bool use_tc = c->p.gemm_mode != FA_GEMM_SIMT && tc_gemm_available();
   if (use_tc) {
     const bool bf16 = is_bf16(c);
@@ -432,7 +432,7 @@ fa_status fa_node_cost(fa_ctx* c, const float* X1, const float* X2, int32_t d,
     FA_STEP(launch_node_cost_simt(n1, n2, L, ldr, R1a, R2a, d, ldx, X1h, X2h,
                                   c->p.alpha, C_node, c->ld, s));
   }
-  // Alg. 1 L5 (reading: A1bar C A2bar^T), k_prop times, as two SpMMs
+  // Algorithm 1, propagation (reading: A1bar C A2bar^T), k_prop times, as two SpMMs
   for (int t = 0; t < c->p.k_prop; ++t) {
     FA_STEP(launch_spmm_left_T(c->g1->d, n2, c->ld, c->ld1, c->g1->d.val_row,
                                nullptr, nullptr, C_node, false, c->Wt, s));

@@ -1,4 +1,4 @@
-// Node-similarity cost on CUDA cores (Alg. 1 L4):
+// Node-similarity cost on CUDA cores (Algorithm 1, node cost):
 //   C[i,j] = alpha exp(-<R1_i, R2_j>) + (1-alpha) exp(-<X1h_i, X2h_j>)
 // Plain FP32 tiled GEMM (64x64 tile, 4x4 outputs per thread, two
 // accumulators).  It is the cross-check for the tcgen05 kernel and the

@@ -1,4 +1,4 @@
-// Node-similarity cost on the 5th-generation tensor cores (Alg. 1 L4):
+// Node-similarity cost on the 5th-generation tensor cores (Algorithm 1, node cost):
 //   C[i,j] = alpha exp(-<R1_i, R2_j>) + (1-alpha) exp(-<X1h_i, X2h_j>)
 //
 // Both products are "A B^T" with K-major operands, so they share one

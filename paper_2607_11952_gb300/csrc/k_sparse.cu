@@ -1,12 +1,12 @@
 // Sparse x dense kernels of FastAlign (Section 3.3, "sparsity-aware"):
-//   - RWR positional encoding, Alg. 1 L3 (SpMM with a tall-skinny dense R)
-//   - SDDMM for the intra-network costs C1, C2, Alg. 1 L7
+//   - RWR positional encoding, Algorithm 1 (SpMM with a tall-skinny dense R)
+//   - SDDMM for the intra-network costs C1, C2, Algorithm 1
 //   - the "SpMM on a wide dense matrix" pair  Z = P1 . D . P2^T
-//     (Section 3.4; Alg. 1 L5, L10, L11), split into
+//     (Section 3.4; Algorithm 1 propagation, edge and neighbourhood costs), split into
 //       left:  W  = P1 D   (row gathers of D, stored transposed as W^T)
 //       right: Z  = W P2^T (row gathers of W^T), with a fused epilogue that
-//              either stores Z (C_node propagation, Alg. 1 L5) or assembles
-//              the cost (Alg. 1 L12, Eq. 2) and the log Gibbs kernel of the
+//              either stores Z (C_node propagation, Algorithm 1) or assembles
+//              the cost (Algorithm 1 cost assembly, Eq. 2) and the log Gibbs kernel of the
 //              proximal step.
 // Storing the left product transposed turns both halves of the triple
 // product into coalesced row gathers; the CTA order keeps one column panel
@@ -48,7 +48,7 @@ fa_status launch_exp_vec(int n, const float* x, float* y, cudaStream_t s) {
   return FA_OK;
 }
 
-// ------------------------------------------------------------ RWR (Alg. 1 L3)
+// ------------------------------------------------------------ RWR (Algorithm 1)
 // Rout[i,:] = (1-beta) sum_k Abar[i,k] Rin[k,:]; the beta R^(0) term is
 // added afterwards by k_add_onehot.  Column panels of 128 (one float4 per
 // lane), one warp per row, four neighbour gathers in flight; blockIdx.x runs
@@ -101,7 +101,7 @@ fa_status launch_rwr_step(const DevGraph& g, int L, int64_t ldr, float beta,
   return FA_OK;
 }
 
-// R[nodes[l], l] += value  (the beta R^(0) term; R^(0) is one-hot, Alg. 1 L2)
+// R[nodes[l], l] += value  (the beta R^(0) term; R^(0) is one-hot, Algorithm 1)
 __global__ void k_add_onehot(int L, int64_t ldr, const int32_t* __restrict__ nodes,
                              float value, float* __restrict__ R) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,7 +122,7 @@ fa_status launch_onehot(int n, int L, int64_t ldr, const int32_t* nodes,
   return launch_add_onehot(L, ldr, nodes, 1.0f, R, s);
 }
 
-// ------------------------------------------------------------ SDDMM (Alg. 1 L7)
+// ------------------------------------------------------------ SDDMM (Algorithm 1)
 // out[e] = w[e] * <R[i,:], R[k,:]> for every stored entry e = (i, k); w is
 // Abar (1/deg i) for C1 = (R1 R1^T) .* Abar1 or Abar^T (1/deg k) for
 // C2 = (R2 R2^T) .* Abar2^T.  One warp per row, lanes over the L columns.
@@ -520,7 +520,7 @@ __device__ __forceinline__ void right_accumulate(
   }
 }
 
-// C_node propagation (Alg. 1 L5): plain store of Z.
+// C_node propagation (Algorithm 1): plain store of Z.
 __global__ void __launch_bounds__(256) k_spmm_right_prop(
     int n1, int n2, int64_t ldw, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const float* __restrict__ qa,
@@ -553,7 +553,7 @@ fa_status launch_spmm_right_prop(const DevGraph& g2, int n1, int64_t ldw,
   return FA_OK;
 }
 
-// Cost assembly + log Gibbs kernel (Alg. 1 L10-L12, Eq. 2, proximal step):
+// Cost assembly + log Gibbs kernel (Phase 2 of Algorithm 1, Eq. 2, proximal step):
 //   C   = C_node + lam_e Z_e - lam_n log max(Z_n, delta) + lam_a C_anc
 //   x   = -C/eps + (lam_p/eps) (log u_i + log K_prev_ij + log v_j)
 // stored as float32, plus the per-(row, 64-column tile) maximum of x.

@@ -1,4 +1,4 @@
-// Fused Sinkhorn sweep, warp-specialised form (Algorithm 1 L13-L16, Eq. 3).
+// Fused Sinkhorn sweep, warp-specialised form (Phase 3 of Algorithm 1, Eq. 3).
 //
 // Same arithmetic and data flow as k_sweep (one read of K per full
 // iteration; a thread-block cluster of Q CTAs owns a row, CTA q the column

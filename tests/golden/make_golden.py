@@ -10,7 +10,7 @@ with a chord 0-2, a tail 3-4-5 and a pendant 6 on node 1; G2 is G1
 relabelled by PERM with the chord 0-2 replaced by the edge 4-6 (in G1's
 labels); 3-dim attributes X1 by hand and X2 = X1 relabelled plus a fixed
 perturbation; two anchors.  Outputs (Algorithm 1 with the oracle's
-default parameters): C_node after propagation (Alg. 1 L4-L5), log S after
+default parameters): C_node after propagation (Algorithm 1, Phase 1), log S after
 one outer iteration of 30 Sinkhorn iterations and after three (Eq. 3-4),
 and the top-1 column of every row of the final plan.
 """

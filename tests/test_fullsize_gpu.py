@@ -3,7 +3,7 @@ configuration bench.py times (default sweep shape, BF16 kernel storage, the
 learned warm start), through the C ABI.
 
 * Sampled rows of the first outer iteration's row-stabilised Gibbs kernel
-  (Alg. 1 L1-L12 from the independent coupling) against the FP64 row oracle
+  (Phases 1-2 of Algorithm 1 from the independent coupling) against the FP64 row oracle
   (oracle/rows_ref.py), FP32 and BF16 storage.
 * Sinkhorn to 1e-4 (Eq. 3): row and column marginals recomputed
   independently in float64 from the stored K and the potentials; the

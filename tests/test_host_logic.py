@@ -1,7 +1,7 @@
 """Host logic of the library, checked on the CPU through its C ABI (no
 device work is involved in either entry point).
 
-* fa_graph_csr_host, the host half of fa_build_graph (Alg. 1 L1), against
+* fa_graph_csr_host, the host half of fa_build_graph (Algorithm 1, row normalisation), against
   the oracle's row-normalised adjacency built by SciPy: identical row
   pointers and column indices, Abar values equal to float32(1/deg_i) and
   Abar^T values equal to float32(1/deg_k), on edge lists with duplicates,

@@ -21,7 +21,7 @@ def _adj_lists(n, edges):
     return [sorted(s) for s in nb]
 
 
-# ------------------------------------------------------------ Alg. 1 L1
+# ------------------------------------------------------------ row normalisation
 
 def test_row_normalized_hand_example():
     # path 0-1-2, a duplicate edge, a self-loop and an isolated node 3
@@ -44,7 +44,7 @@ def test_row_normalized_rows_sum_to_one_or_zero():
     assert np.all(s[deg == 0] == 0)
 
 
-# ------------------------------------------------------------ Alg. 1 L2-L3
+# ------------------------------------------------------------ RWR
 
 def test_rwr_one_step_hand_value():
     A = R.row_normalized(3, np.array([[0, 1], [1, 2]]))
@@ -66,7 +66,7 @@ def test_rwr_converges_to_ppr_solve():
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
 
 
-# ------------------------------------------------------------ Alg. 1 L4
+# ------------------------------------------------------------ node cost
 
 def test_initial_node_cost_hand_values():
     # R = 0 -> exp(0) = 1; features e_0, e_1 -> cosine matrix = I
@@ -94,7 +94,7 @@ def test_node_cost_brute_force():
             assert abs(C[i, j] - (0.5 * math.exp(-rr) + 0.5 * math.exp(-cos))) < 1e-14
 
 
-# ------------------------------------------------------------ Alg. 1 L5
+# ------------------------------------------------------------ propagation
 
 def test_propagation_is_double_neighbourhood_mean():
     rng = synth.rng_for(11)
@@ -114,7 +114,7 @@ def test_propagation_is_double_neighbourhood_mean():
             assert abs(got[i, j] - want) < 1e-14
 
 
-# ------------------------------------------------------------ Alg. 1 L6
+# ------------------------------------------------------------ anchor cost
 
 def test_anchor_cost_values():
     Ca = R.anchor_cost(3, 4, np.array([[0, 2], [2, 1]]), 0.05)
@@ -125,7 +125,7 @@ def test_anchor_cost_values():
     np.testing.assert_allclose(Ca[mask], -math.log(0.05))
 
 
-# ------------------------------------------------------------ Alg. 1 L7, L10, L11
+# ------------------------------------------------------------ intra-graph, edge and neighbourhood costs
 
 def _small_pair(seed=5, n1=24, n2=20):
     rng = synth.rng_for(seed)
@@ -360,7 +360,7 @@ def test_planted_permutation_is_recovered():
     out = R.fastalign(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors,
                       R.Params(k_prop=0), 5, 50)
     assert R.hits_mrr(np.exp(out["logS"]), g.test_pairs)["hits@1"] == 1.0
-    # With the propagation step (Alg. 1 L5) each node's own attribute cost
+    # With the propagation step of Algorithm 1 each node's own attribute cost
     # is replaced by its neighbourhood mean, so nodes with (nearly)
     # identical neighbourhoods can swap; every miss must still rank 2-3.
     out = R.fastalign(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors,

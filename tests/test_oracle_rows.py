@@ -1,6 +1,6 @@
 """Pins of the row-restricted oracle (oracle/rows_ref.py) against the
 whole-matrix oracle: the first outer iteration's row-stabilised Gibbs
-kernel, Alg. 1 L1-L12 from the independent coupling, must agree row by row
+kernel, Phases 1-2 of Algorithm 1 from the independent coupling, must agree row by row
 to rounding (1e-12), for k_C = 0, 1, 2 and with anchors on the sampled rows."""
 import numpy as np
 import pytest
