@@ -289,7 +289,7 @@ fa_status fa_vec_axpby(int32_t n, float a, const float* x, float b,
 
 /*
  * fa_plan_change -- how far the plan moved between two outer iterations,
- * the convergence test of Algorithm 1's outer loop ("until S converges";
+ * the convergence test of Algorithm 1's outer loop (repeat until the plan converges;
  * reading: the L1 distance of the plans):
  *     *l1_out = sum_ij | T_a,ij - T_b,ij |,
  *     T = diag(exp(log_u)) K diag(exp(log_v)).

@@ -275,7 +275,7 @@ def sinkhorn_scaling(K: np.ndarray, mu: np.ndarray, nu: np.ndarray, n_iter: int,
 
 def plan_l1(logS_a: np.ndarray, logS_b: np.ndarray) -> float:
     """How far the plan moved between two outer iterations, the test of
-    Algorithm 1's outer loop ("until S converges"), read as the L1
+    Algorithm 1's outer loop (repeat until the plan converges), read as the L1
     distance sum_ij |S_a,ij - S_b,ij| of the plans given as log S."""
     return float(np.abs(np.exp(logS_a) - np.exp(logS_b)).sum())
 

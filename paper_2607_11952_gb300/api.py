@@ -215,7 +215,7 @@ class Aligner:
         status[, plan change]).
 
         plan_tol: stop before n_outer once an outer iteration moves the plan
-        by at most plan_tol in L1 (the outer loop's "until S converges").
+        by at most plan_tol in L1 (the outer loop's convergence test).
         checkpoint: write a checkpoint after every outer iteration.
         resume: continue from a checkpoint (Phase 1 is recomputed)."""
         self.node_cost(X1, X2, anchors)
