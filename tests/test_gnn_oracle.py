@@ -60,3 +60,14 @@ def test_adam_constant_gradient_closed_form():
         theta, m, v = G.adam_step(theta, m, v, g, t, lr=0.1)
     # with a constant gradient the bias-corrected step is lr * sign(g)
     np.testing.assert_allclose(theta, -0.5 * np.sign(g) * (g != 0), atol=1e-7)
+
+
+def test_features_hand_values():
+    # degrees (0, 1, 3); log v1 (1, 2, 6) has mean 3; c_prev (0.5, 0.5, 2)
+    # has mean 1; the third input is log(1 + degree)
+    F = G.features(np.array([0, 1, 3]), np.array([1.0, 2.0, 6.0]),
+                   np.array([0.5, 0.5, 2.0]))
+    want = np.array([[-2.0, -0.5, 0.0],
+                     [-1.0, -0.5, np.log(2.0)],
+                     [3.0, 1.0, np.log(4.0)]])
+    np.testing.assert_allclose(F, want, rtol=0, atol=1e-15)

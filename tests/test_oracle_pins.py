@@ -388,3 +388,70 @@ def test_plan_l1_definition():
     brute = sum(abs(S[i, j] - T[i, j]) for i in range(3) for j in range(4))
     assert abs(R.plan_l1(np.log(S), np.log(T)) - brute) < 1e-15
     assert R.plan_l1(np.log(S), np.log(T)) <= 2.0
+
+
+# ------------------------------------------------------------ proximal outer loop
+
+def _pure_node_cost_run(n1, n2, e1, e2, X1, X2, eps, lam_p, n_outer):
+    """The oracle's outer loop with the structural, neighbourhood and anchor
+    weights switched off, so every outer iteration sees the same cost
+    C = C_node and only the proximal term links consecutive solves."""
+    p = R.Params(eps=eps, lam_p=lam_p, lam_e=0.0, lam_n=0.0, lam_a=0.0, k_prop=0)
+    anchors = np.zeros((0, 2), np.int64)
+    out = R.fastalign(n1, n2, e1, e2, X1, X2, anchors, p, n_outer, 40000,
+                      tol=1e-14, check_every=1)
+    assert all(h["errs"][-1] <= 1e-14 for h in out["hist"])   # every solve converged
+    return out, out["phase1"].C_node
+
+
+def _prox_temperature(eps, lam_p, t):
+    """Effective temperature after t proximal steps on a fixed cost.  Section
+    3.1's proximal point step with the KL term of reading R-prox gives
+    S_t = diag(x) exp(-C/eps - (lam_p/eps) (C/eta_{t-1})) diag(y), i.e.
+    1/eta_t = 1/eps + (lam_p/eps) / eta_{t-1}, starting from the constant
+    plan (1/eta_0 = 0).  With lam_p = eps this is eta_t = eps / t."""
+    inv = 0.0
+    for _ in range(t):
+        inv = 1.0 / eps + (lam_p / eps) * inv
+    return 1.0 / inv
+
+
+@pytest.mark.parametrize("lam_ratio", [1.0, 0.5, 2.0])
+def test_proximal_outer_loop_matches_2x2_closed_form(lam_ratio):
+    """Fixed cost, 2 x 2: after t outer iterations the plan is the entropic
+    optimum of C at the temperature eta_t of the proximal recursion, whose
+    closed form is the 2 x 2 root above.  A flipped sign of the proximal
+    term, or lam_p entering without its 1/eps weight, changes eta_t."""
+    rng = np.random.default_rng(40)
+    X1 = rng.standard_normal((2, 3))
+    X2 = rng.standard_normal((2, 3))
+    e = np.array([[0, 1]])
+    eps = 0.5
+    mu = nu = np.array([0.5, 0.5])
+    for t in (1, 2, 3, 4):
+        out, C = _pure_node_cost_run(2, 2, e, e, X1, X2, eps, lam_ratio * eps, t)
+        eta = _prox_temperature(eps, lam_ratio * eps, t)
+        want = _closed_form_2x2(C, mu, nu, eta)
+        np.testing.assert_allclose(np.exp(out["logS"]), want, rtol=0, atol=1e-12)
+
+
+def test_proximal_outer_loop_is_one_solve_at_eps_over_t():
+    """Fixed cost on a 9 x 7 pair with lam_p = eps: t outer iterations equal
+    a single entropic OT solve of C at eps / t (and differ from the solve at
+    eps, so the pin is not vacuous)."""
+    rng = synth.rng_for(41)
+    n1, n2 = 9, 7
+    e1 = synth.erdos_renyi(n1, 2.5, rng)
+    e2 = synth.erdos_renyi(n2, 2.5, rng)
+    X1 = rng.standard_normal((n1, 4))
+    X2 = rng.standard_normal((n2, 4))
+    eps = 0.1
+    mu, nu = np.full(n1, 1 / n1), np.full(n2, 1 / n2)
+    for t in (2, 3, 5):
+        out, C = _pure_node_cost_run(n1, n2, e1, e2, X1, X2, eps, eps, t)
+        a, b, errs, _ = R.sinkhorn_log(C, mu, nu, eps / t, 40000, tol=1e-14)
+        want = np.exp(R.plan_log(C, a, b, eps / t))
+        got = np.exp(out["logS"])
+        np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-14)
+        a1, b1, _, _ = R.sinkhorn_log(C, mu, nu, eps, 40000, tol=1e-14)
+        assert np.abs(got - np.exp(R.plan_log(C, a1, b1, eps))).max() > 1e-3
