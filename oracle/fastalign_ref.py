@@ -257,20 +257,37 @@ def marginal_error(logK, a, b, mu, nu, eps) -> float:
 
 
 def sinkhorn_scaling(K: np.ndarray, mu: np.ndarray, nu: np.ndarray, n_iter: int,
-                     u0: np.ndarray | None = None):
+                     u0: np.ndarray | None = None, v0: np.ndarray | None = None,
+                     tol: float | None = None, check_every: int = 1,
+                     track_err: bool = True):
     """Scaling-domain Sinkhorn, the exponentiated form of Eq. 3 with
     u = exp(b/eps), v = exp(a/eps): v = nu / (K^T u), then u = mu / (K v).
     Same iteration order and initial u as ``sinkhorn_log`` when K is the
-    row-stabilised kernel and u0 = 1.  Returns (u, v, errs)."""
+    row-stabilised kernel and u0 = 1.  If ``v0`` is given (a column scaling
+    already updated, like ``a_init`` of ``sinkhorn_log``) the first
+    iteration skips its v update.  Stops after n_iter iterations, or at the
+    first checked iteration whose marginal error (R-order) is <= tol.
+    Returns (u, v, errs) and, when tol is given, the iteration count too."""
     u = np.ones(K.shape[0]) if u0 is None else np.asarray(u0, np.float64).copy()
     v = None
     errs = []
-    for _ in range(n_iter):
-        v = nu / (K.T @ u)
+    it = 0
+    for it in range(1, n_iter + 1):
+        if it == 1 and v0 is not None:
+            v = np.asarray(v0, np.float64).copy()
+        else:
+            v = nu / (K.T @ u)
         u = mu / (K @ v)
-        S_col = v * (K.T @ u)
-        errs.append(float(np.abs(S_col - nu).sum() + np.abs(u * (K @ v) - mu).sum()))
-    return u, v, np.asarray(errs)
+        checked = tol is not None and (it % check_every == 0 or it == n_iter)
+        if track_err or checked:
+            S_col = v * (K.T @ u)
+            e = float(np.abs(S_col - nu).sum() + np.abs(u * (K @ v) - mu).sum())
+            errs.append(e)
+            if checked and e <= tol:
+                break
+    if tol is None:
+        return u, v, np.asarray(errs)
+    return u, v, np.asarray(errs), it
 
 
 def plan_l1(logS_a: np.ndarray, logS_b: np.ndarray) -> float:
@@ -332,15 +349,24 @@ def outer_step(ph: Phase1, logS_prev: np.ndarray, p: Params):
 
 def fastalign(n1, n2, edges1, edges2, X1, X2, anchors, p: Params,
               n_outer: int, n_sink: int, tol: float | None = None,
-              check_every: int = 1, ph: Phase1 | None = None):
+              check_every: int = 1, ph: Phase1 | None = None,
+              sinkhorn: str = "log"):
     """Algorithm 1 end to end: Phase 1 once, then n_outer rounds of Phase 2
     (S-dependent costs) and Phase 3 (Sinkhorn, Eq. 3), recovering S by Eq. 4.
     The plan is carried as log S in float64 so nothing underflows.
 
-    Returns a dict with the final log S, the last potentials and, per outer
-    iteration, the Sinkhorn errors and iteration counts."""
+    sinkhorn="log" solves each outer iteration with the log-domain updates
+    of Eq. 3; sinkhorn="scaling" with their exponentiated form on the
+    row-stabilised kernel exp(log K - max_j log K) (reading R-b0: u = 1 is
+    the stabilising b0), the same iterates in exact arithmetic and the form
+    timed as the CPU baseline.
+
+    Returns a dict with the final log S, the last potentials (log form)
+    and, per outer iteration, the Sinkhorn errors and iteration counts."""
     if ph is None:
         ph = phase1(n1, n2, edges1, edges2, X1, X2, anchors, p)
+    if sinkhorn not in ("log", "scaling"):
+        raise ValueError(sinkhorn)
     mu = np.full(n1, 1.0 / n1)
     nu = np.full(n2, 1.0 / n2)
     logS = np.full((n1, n2), -math.log(n1 * n2))        # reading R-init
@@ -348,9 +374,22 @@ def fastalign(n1, n2, edges1, edges2, X1, X2, anchors, p: Params,
     a = b = None
     for _ in range(n_outer):
         C_eff = outer_step(ph, logS, p)
-        a, b, errs, its = sinkhorn_log(C_eff, mu, nu, p.eps, n_sink, tol=tol,
-                                       check_every=check_every)
-        logS = plan_log(C_eff, a, b, p.eps)
+        if sinkhorn == "log":
+            a, b, errs, its = sinkhorn_log(C_eff, mu, nu, p.eps, n_sink, tol=tol,
+                                           check_every=check_every)
+            logS = plan_log(C_eff, a, b, p.eps)
+        else:
+            logK = -C_eff / p.eps
+            m = np.max(logK, axis=1, keepdims=True)
+            Ks = np.exp(logK - m)
+            # without tol only the last iteration's error is recorded
+            u, v, errs, its = sinkhorn_scaling(
+                Ks, mu, nu, n_sink, tol=tol if tol is not None else -1.0,
+                check_every=check_every if tol is not None else n_sink,
+                track_err=False)
+            logS = np.log(u)[:, None] + (logK - m) + np.log(v)[None, :]
+            b = p.eps * (np.log(u) - m[:, 0])     # (a_j + b_i)/eps = log u_i - m_i + log v_j
+            a = p.eps * np.log(v)
         hist.append(dict(errs=errs, iters=its))
     return dict(logS=logS, a=a, b=b, hist=hist, phase1=ph)
 

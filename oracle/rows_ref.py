@@ -170,3 +170,67 @@ def first_kernel_rows_from(st: Phase1Rows, anchors, p: R.Params, rows,
     logS0 = np.log(mu)[rows][:, None] + np.log(nu)[None, :]
     x = -(C - p.lam_p * logS0) / p.eps
     return np.exp(x - x.max(axis=1, keepdims=True))
+
+
+def _c_intra_matrix(A: sp.csr_matrix, R_: np.ndarray, transpose: bool) -> sp.csr_matrix:
+    """C1 = (R1 R1^T) .* A1bar, or C2 = (R2 R2^T) .* A2bar^T (transpose=True)
+    (Algorithm 1, intra-graph costs), evaluated only on the stored entries
+    of the adjacency; the definition is the same as the dense-then-masked
+    one of ``fastalign_ref.intra_costs``."""
+    M = (A.T if transpose else A).tocoo()
+    dots = np.einsum("ij,ij->i", R_[M.row], R_[M.col])
+    return sp.csr_matrix((M.data * dots, (M.row, M.col)), shape=M.shape)
+
+
+def kernel_rows_from_plan(st: Phase1Rows, anchors, p: R.Params, rows,
+                          plan_rows, operands: str = "f64"):
+    """Rows ``rows`` of the row-stabilised Gibbs kernel of an outer iteration
+    whose previous plan S_prev is general (Phases 1-2 of Algorithm 1 with the
+    proximal step of reading R-prox).
+
+    ``plan_rows(ks)`` returns the float64 rows ks of S_prev (len(ks) x n2).
+    Each quantity is its definition at the requested rows:
+      C_edge[i, :] = (sum_k C1[i, k] S_prev[k, :]) C2^T,
+      C_nbr[i, :]  = -log(max((sum_k A1bar[k, i] S_prev[k, :]) A2bar, delta)),
+      C_eff[i, :]  = C_node + lam_e C_edge + lam_n C_nbr + lam_a C_anc
+                     - lam_p log S_prev[i, :],
+    then x = -C_eff / eps and K[i, :] = exp(x - max_j x) (reading R-b0).
+    A1bar is symmetric in pattern (undirected graphs), so the k with
+    A1bar[k, i] != 0 are the neighbours of i, with weight 1/deg(k)."""
+    rows = [int(i) for i in rows]
+    n1, n2, A1, A2 = st.n1, st.n2, st.A1, st.A2
+    R1, R2, X1h, X2h = st.R1, st.R2, st.X1h, st.X2h
+    if operands == "bf16":
+        g1, g2, f1, f2 = bf16_round(R1), bf16_round(R2), bf16_round(X1h), bf16_round(X2h)
+    elif operands == "f64":
+        g1, g2, f1, f2 = R1, R2, X1h, X2h
+    else:
+        raise ValueError(operands)
+    C_node = _propagated_rows(rows, A1, A2, g1, g2, f1, f2, p.alpha, p.k_prop)
+    C1 = _c_intra_matrix(A1, R1, transpose=False)
+    C2 = _c_intra_matrix(A2, R2, transpose=True)
+    A1T = A1.T.tocsr()
+    out = np.empty((len(rows), n2))
+    H = np.zeros(n2)
+    anc = np.asarray(anchors, dtype=np.int64).reshape(-1, 2)
+    for t, i in enumerate(rows):
+        # left products: row i of C1 S_prev and of A1bar^T S_prev
+        lo, hi = C1.indptr[i], C1.indptr[i + 1]
+        ks = C1.indices[lo:hi]
+        Sk = plan_rows(ks) if ks.size else np.zeros((0, n2))
+        y_e = C1.data[lo:hi] @ Sk if ks.size else np.zeros(n2)
+        lo2, hi2 = A1T.indptr[i], A1T.indptr[i + 1]
+        ks2 = A1T.indices[lo2:hi2]
+        Sk2 = Sk if np.array_equal(ks2, ks) else (plan_rows(ks2) if ks2.size else np.zeros((0, n2)))
+        y_n = A1T.data[lo2:hi2] @ Sk2 if ks2.size else np.zeros(n2)
+        # right products: (.) C2^T and (.) A2bar
+        z_e = C2 @ y_e
+        z_n = A2.T @ y_n
+        H[:] = 0.0
+        H[anc[anc[:, 0] == i, 1]] = 1.0
+        C = (C_node[t] + p.lam_e * z_e - p.lam_n * np.log(np.maximum(z_n, p.delta))
+             + p.lam_a * (-np.log(p.eps_anc + H)))
+        logS_i = np.log(plan_rows(np.array([i]))[0])
+        x = -(C - p.lam_p * logS_i) / p.eps
+        out[t] = np.exp(x - x.max())
+    return out

@@ -455,3 +455,30 @@ def test_proximal_outer_loop_is_one_solve_at_eps_over_t():
         np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-14)
         a1, b1, _, _ = R.sinkhorn_log(C, mu, nu, eps, 40000, tol=1e-14)
         assert np.abs(got - np.exp(R.plan_log(C, a1, b1, eps))).max() > 1e-3
+
+
+@pytest.mark.parametrize("tol", [None, 1e-6])
+def test_scaling_form_of_the_whole_method_matches_log_form(tol):
+    """The two Sinkhorn forms of Eq. 3 inside the full outer loop: with the
+    same iteration counts (or the same stopping rule) they give the same
+    plans, potentials and iteration counts, on an uneven pair over several
+    outer iterations (the proximal term then carries each solve into the
+    next)."""
+    rng = synth.rng_for(43)
+    e1 = synth.chung_lu(80, 2.4, 5.0, rng)
+    g = synth.make_pair(e1, 80, d=8, sigma=0.1, anchor_frac=0.1, frac_del=0.1,
+                        frac_add=0.1, rng=rng, keep_nodes=64)
+    p = R.Params()
+    ph = R.phase1(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, p)
+    kw = dict(tol=tol, check_every=3, ph=ph)
+    lg = R.fastalign(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, p, 4, 60, **kw)
+    sc = R.fastalign(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, p, 4, 60,
+                     sinkhorn="scaling", **kw)
+    np.testing.assert_allclose(np.exp(sc["logS"]), np.exp(lg["logS"]), rtol=1e-10, atol=1e-16)
+    assert [h["iters"] for h in sc["hist"]] == [h["iters"] for h in lg["hist"]]
+    np.testing.assert_allclose(sc["hist"][-1]["errs"][-1], lg["hist"][-1]["errs"][-1],
+                               rtol=1e-8, atol=1e-15)
+    # potentials up to the gauge (a + k, b - k)
+    k = np.mean(sc["a"] - lg["a"])
+    np.testing.assert_allclose(sc["a"] - k, lg["a"], atol=1e-10)
+    np.testing.assert_allclose(sc["b"] + k, lg["b"], atol=1e-10)

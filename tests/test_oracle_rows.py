@@ -92,3 +92,28 @@ def test_bf16_operands_change_only_the_node_products():
     x = -R.outer_step(ph, logS0, p) / p.eps
     K = np.exp(x - x.max(axis=1, keepdims=True))
     np.testing.assert_allclose(K16, K[rows], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("k_prop", [0, 1])
+def test_rows_from_a_general_plan_match_whole_matrix_oracle(k_prop):
+    """The row oracle of an outer iteration whose previous plan is general
+    (not the rank-one first plan), against fastalign_ref's whole-matrix
+    outer step on the same plan; rows with anchors, the highest-degree
+    row and the last row included."""
+    rng = synth.rng_for(79)
+    e1 = synth.chung_lu(90, 2.2, 6.0, rng)
+    g = synth.make_pair(e1, 90, d=8, sigma=0.1, anchor_frac=0.1, frac_del=0.1,
+                        frac_add=0.1, rng=rng, keep_nodes=75)
+    p = R.Params(k_prop=k_prop, lam_e=200.0)
+    ph = R.phase1(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, p)
+    prng = np.random.default_rng(3)
+    S = np.exp(-6.0 * prng.random((g.n1, g.n2)))
+    S /= S.sum()
+    logS = np.log(S)
+    x = -R.outer_step(ph, logS, p) / p.eps
+    K = np.exp(x - x.max(axis=1, keepdims=True))
+    st = rows_ref.prepare(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, p)
+    deg = np.diff(st.A1.indptr)
+    rows = [0, int(np.argmax(deg)), int(g.anchors[0, 0]), g.n1 - 1]
+    Kr = rows_ref.kernel_rows_from_plan(st, g.anchors, p, rows, lambda ks: S[np.asarray(ks)])
+    np.testing.assert_allclose(Kr, K[rows], rtol=1e-11, atol=1e-14)
