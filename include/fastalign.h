@@ -312,14 +312,24 @@ fa_status fa_plan_change(fa_ctx* ctx, const void* K_a, const float* log_u_a,
  * latency-critical loop that cannot afford cudaMalloc's cost and implicit
  * synchronisation.  It needs no fa_ctx (creating one allocates).
  *
- * Computes, exactly as one iteration of fa_sinkhorn: u_i = mu_i /
+ * Computes, with the arithmetic of one fa_sinkhorn iteration: u_i = mu_i /
  * sum_j K_ij v_j (log_u, n1), the next column scaling from the column sums
  * sum_i K_ij u_i (log_v_next, n2) and the L1 column-marginal error of the
  * plan (log_u, log_v) into *err (device double), with mu = 1/n1 and
- * nu = 1/n2.  K: device, n1 x ld, FA_F32 or FA_BF16 (dtype), 16-byte
- * aligned, padding columns 0; log_v, log_u, log_v_next, err: device.
+ * nu = 1/n2.  The partial column sums may be grouped over fewer row groups
+ * than fa_sinkhorn uses (the static array bounds them), so results agree
+ * with fa_sinkhorn up to FP32 summation order, not bit for bit.
+ * K: device, n1 x ld, FA_F32 or FA_BF16 (dtype), 16-byte aligned, padding
+ * columns 0; log_v, log_u, log_v_next, err: device.
  * status (device int32, nullable) receives the kernels' status bits
- * (1: NaN/Inf or an all-zero row or column, 2: a bounded wait gave up).
+ * (1: NaN/Inf or an all-zero row or column, 2: a bounded wait gave up);
+ * the call itself returns before the kernels run, so it cannot report
+ * them.  With status == NULL the bits go to a static word nobody reads:
+ * they are lost, and a NaN or a timed-out wait goes unnoticed -- pass a
+ * status word to learn of them.
+ * The launch shape is planned on the first call for each (device, n1, ld,
+ * dtype) and reused by later calls (the FA_SWEEP_* tuning variables are
+ * read at that first call only).
  *
  * Scratch: file-scope static device arrays reserved when the library is
  * loaded (8 MiB of partial column sums plus small counters) and held by

@@ -30,13 +30,24 @@ CHECKPOINT_FORMAT = "fastalign-checkpoint-1"
 
 
 def write_checkpoint(path: str, state: dict) -> None:
-    """Write an outer-loop checkpoint atomically: the file is written under a
-    temporary name beside ``path`` and renamed over it, so an interruption
-    leaves the previous checkpoint intact."""
+    """Write an outer-loop checkpoint atomically and durably: the file is
+    written under a temporary name beside ``path``, flushed to the storage
+    device (fsync), renamed over ``path``, and the directory entry is
+    flushed too.  An interruption at any point -- the process killed, or
+    the machine losing power -- leaves either the previous checkpoint or the
+    new one, never a truncated file under ``path``."""
     tmp = f"{path}.tmp.{os.getpid()}"
     try:
-        torch.save({"format": CHECKPOINT_FORMAT, **state}, tmp)
+        with open(tmp, "wb") as f:
+            torch.save({"format": CHECKPOINT_FORMAT, **state}, f)
+            f.flush()
+            os.fsync(f.fileno())
         os.replace(tmp, path)
+        d = os.open(os.path.dirname(os.path.abspath(path)), os.O_RDONLY)
+        try:
+            os.fsync(d)
+        finally:
+            os.close(d)
     finally:
         if os.path.exists(tmp):
             os.remove(tmp)
@@ -190,19 +201,31 @@ class Aligner:
                                 stream)
 
     # -- checkpoint / resume of the outer loop
-    def save_checkpoint(self, path: str, t: int, extra: dict | None = None):
+    def save_checkpoint(self, path: str, t: int, extra: dict | None = None,
+                        warm=None):
         """Write the state an interrupted alignment resumes from: the Gibbs
-        kernel K, the log-scalings and the number t of outer iterations done.
-        C_node is not saved (fa_node_cost recomputes it deterministically)."""
-        write_checkpoint(path, {"n1": self.n1, "n2": self.n2, "ld": self.ld,
-                                "dtype": self.params.dtype, "t": int(t),
-                                "K": self.K.cpu(), "log_u": self.log_u.cpu(),
-                                "log_v": self.log_v.cpu(), "extra": extra or {}})
+        kernel K, the log-scalings, the number t of outer iterations done
+        and, with a warm starter, its carried state (the previous solve's
+        correction), without which a resumed warm-started run would not
+        repeat the uninterrupted one.  C_node is not saved (fa_node_cost
+        recomputes it deterministically)."""
+        state = {"n1": self.n1, "n2": self.n2, "ld": self.ld,
+                 "dtype": self.params.dtype, "t": int(t),
+                 "K": self.K.cpu(), "log_u": self.log_u.cpu(),
+                 "log_v": self.log_v.cpu(), "extra": extra or {}}
+        if warm is not None and hasattr(warm, "state"):
+            state["warm"] = warm.state()
+        write_checkpoint(path, state)
 
-    def load_checkpoint(self, path: str) -> int:
-        """Restore K and the log-scalings written by save_checkpoint; returns
-        the number of outer iterations they hold."""
+    def load_checkpoint(self, path: str, warm=None) -> int:
+        """Restore K and the log-scalings written by save_checkpoint (and a
+        warm starter's state, when one is given and was saved); returns the
+        number of outer iterations they hold."""
         ck = read_checkpoint(path, self.n1, self.n2, self.ld, self.params.dtype)
+        if warm is not None and hasattr(warm, "load_state"):
+            if "warm" not in ck:
+                raise ValueError("checkpoint holds no warm-start state")
+            warm.load_state(ck["warm"])
         self.K.copy_(ck["K"])
         self.log_u.copy_(ck["log_u"])
         self.log_v.copy_(ck["log_v"])
@@ -214,14 +237,20 @@ class Aligner:
         """Algorithm 1 end to end; returns per-outer (iterations, error,
         status[, plan change]).
 
+        warm: None (cold start), a warm starter (an object with ``solve``,
+        such as gnn.WarmStarter, which runs its own before/after-solve steps
+        and the cold-start fallback), or a callable warm(aligner) returning
+        the warm column scaling for fa_sinkhorn.
         plan_tol: stop before n_outer once an outer iteration moves the plan
         by at most plan_tol in L1 (the outer loop's convergence test).
-        checkpoint: write a checkpoint after every outer iteration.
+        checkpoint: write a checkpoint after every outer iteration (with the
+        warm starter's state).
         resume: continue from a checkpoint (Phase 1 is recomputed)."""
+        starter = warm if hasattr(warm, "solve") else None
         self.node_cost(X1, X2, anchors)
         t0 = 0
         if resume is not None:
-            t0 = self.load_checkpoint(resume)
+            t0 = self.load_checkpoint(resume, warm=starter)
         else:
             self.plan_init()
         prev = None
@@ -233,10 +262,13 @@ class Aligner:
         hist = []
         for t in range(t0, n_outer):
             self.align_iter()
-            w = warm(self) if warm is not None else None
-            it, err, st = self.sinkhorn(n_sink, tol, check_every, w)
+            if starter is not None:
+                it, err, st, _ = starter.solve(n_sink, tol, check_every)
+            else:
+                w = warm(self) if warm is not None else None
+                it, err, st = self.sinkhorn(n_sink, tol, check_every, w)
             if checkpoint is not None:
-                self.save_checkpoint(checkpoint, t + 1)
+                self.save_checkpoint(checkpoint, t + 1, warm=starter)
             if prev is None:
                 hist.append((it, err, st))
                 continue

@@ -8,6 +8,8 @@
 // addresses.
 #include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "fa_internal.cuh"
 
@@ -35,6 +37,17 @@ constexpr int kMaxDevices = 128;
 static std::mutex g_static_mu;
 static bool g_static_ready[kMaxDevices] = {};
 static StaticScratch g_static_ptrs[kMaxDevices];
+
+// Sweep shapes already planned, per (device, n1, ld, storage type): the
+// entry is meant for loops of many calls, so the host-side planning and
+// the occupancy query run once per shape, not on every call.
+struct PlanKey {
+  int dev;
+  int32_t n1;
+  int64_t ld;
+  bool bf16;
+};
+static std::vector<std::pair<PlanKey, SweepPlan>> g_static_plans;
 
 // Device addresses of the static scratch on the current device, looked up
 // once per device (the first call on a device does it).
@@ -98,12 +111,29 @@ extern "C" fa_status fa_sinkhorn_step_static(const void* K, int32_t dtype, int32
   FA_CUDA(cudaMemsetAsync(P.ticket, 0, sizeof(unsigned), s));
   FA_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
   const bool bf16 = dtype == FA_BF16;
-  // as many row groups as clusters fit on the device at once, bounded by
-  // the rows of partial column sums the static array holds
-  SweepPlan sp = plan_sweep(n1, ld, bf16, 1 << 20);
-  const int resident = sp.Q >= 1 ? sweep_max_active_clusters(sp, bf16) : 0;
-  const int max_G = (int)std::min<int64_t>(std::max(1, resident), kStaticColpart / ld);
-  sp = plan_sweep(n1, ld, bf16, max_G);
+  int dev = 0;
+  FA_CUDA(cudaGetDevice(&dev));
+  SweepPlan sp;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    for (const auto& e : g_static_plans)
+      if (e.first.dev == dev && e.first.n1 == n1 && e.first.ld == ld && e.first.bf16 == bf16) {
+        sp = e.second;
+        have = true;
+        break;
+      }
+  }
+  if (!have) {
+    // as many row groups as clusters fit on the device at once, bounded by
+    // the rows of partial column sums the static array holds
+    sp = plan_sweep(n1, ld, bf16, 1 << 20);
+    const int resident = sp.Q >= 1 ? sweep_max_active_clusters(sp, bf16) : 0;
+    const int max_G = (int)std::min<int64_t>(std::max(1, resident), kStaticColpart / ld);
+    sp = plan_sweep(n1, ld, bf16, max_G);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    g_static_plans.push_back({PlanKey{dev, n1, ld, bf16}, sp});
+  }
   FA_TRY(launch_sweep(sp, n1, n2, ld, K, bf16, log_v, log_u, 1.0f / (float)n1, P.colpart, st, s));
   FA_TRY(launch_col_finalize(n2, ld, sp.G, P.colpart, log_v, 1.0f / (float)n2, log_v_next,
                              P.err_part, P.ticket, err, st, s));

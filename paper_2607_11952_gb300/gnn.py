@@ -147,6 +147,16 @@ class WarmStarter:
     def after_solve(self):
         L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, -1.0, self.log_v1, self.corr)
 
+    def state(self) -> dict:
+        """What the next solve depends on besides the plan: the previous
+        solve's correction (host copy, for checkpoints)."""
+        return {"mode": self.mode, "corr": self.corr.cpu()}
+
+    def load_state(self, st: dict) -> None:
+        if st.get("mode") != self.mode or tuple(st["corr"].shape) != tuple(self.corr.shape):
+            raise ValueError("warm-start state of another mode or size")
+        self.corr.copy_(st["corr"])
+
     def solve(self, max_iter: int, tol: float, check_every: int = 5):
         """One warm-started solve; if it meets NaN/Inf (a bad prediction),
         the cold start runs from the same kernel instead.  Returns

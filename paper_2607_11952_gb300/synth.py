@@ -279,3 +279,19 @@ def bf16_representable(x: np.ndarray) -> np.ndarray:
     u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
     return r.view(np.float32)
+
+
+def random_kernel_rows(n_rows: int, n2: int, rng: np.random.Generator,
+                       spread: float = 10.0) -> np.ndarray:
+    """A block of rows of a seeded positive n_rows x n2 matrix with entries
+    exp(-spread U), U uniform on [0, 1), rounded onto the bfloat16 grid
+    (float32 array), so FP32 and BF16 storage of it hold the same values.
+    Stands in for a Gibbs kernel where a test needs a general one."""
+    u = rng.random((n_rows, n2), dtype=np.float32)
+    return bf16_representable(np.exp(-np.float32(spread) * u))
+
+
+def random_log_scalings(n: int, rng: np.random.Generator, sd: float = 0.5) -> np.ndarray:
+    """Seeded log-scalings -log(n) + N(0, sd^2) (float32): a vector whose
+    exponentials have the magnitude of a marginal 1/n."""
+    return (-math.log(n) + sd * rng.standard_normal(n)).astype(np.float32)

@@ -1,0 +1,82 @@
+"""The plain FP32 method on the 10k Chung-Lu pair (exponent 2.5, mean degree
+8, 10% edge noise, 64-dim attributes, 5% anchors; 20 outer iterations x 100
+Sinkhorn iterations), through the C ABI, against the whole FP64 oracle run
+on the same seeded pair (Algorithm 1 end to end, Eq. 3 in its scaling form,
+which the oracle's CPU tests pin to the log form over whole runs).
+
+Tolerances (the FP32 path's, written here):
+* plan: ||T - T_ref||_F / ||T_ref||_F <= 1e-4;
+* column marginals: |m - m_ref|_inf <= 1e-6 / n2 + 1e-6 max m_ref (1e-6
+  relative to 1/n); row marginals within 1e-6 / n1 of mu (rows are exact
+  after the b update up to FP32 rounding of the row sums);
+* top-10 indices identical in every row whose relative score gaps
+  (T_(k) - T_(k+1)) / T_(1), k = 1..10, all exceed 1e-5;
+* Hits@1 within one test pair of the oracle's."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fastalign_ref as R  # noqa: E402
+from paper_2607_11952_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+OUTER, SINK = 20, 100
+
+
+@pytest.fixture(scope="module")
+def runs():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_11952_gb300 import api
+    g = synth.config_pair("cl10k")
+    t0 = time.perf_counter()
+    ref = R.fastalign(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors,
+                      R.Params(), OUTER, SINK, sinkhorn="scaling")
+    t_ref = time.perf_counter() - t0
+    al = api.Aligner(api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2),
+                     api.Params(dtype="f32"))
+    try:
+        hist = al.align(g.X1, g.X2, g.anchors, n_outer=OUTER, n_sink=SINK)
+        idx, _ = al.topk(10)
+        torch.cuda.synchronize()
+        T = al.plan_f64()
+        out = dict(T=T, idx=idx.cpu().numpy(), hist=hist,
+                   hits=al.hits_mrr(g.test_pairs))
+    finally:
+        al.close()
+    print(f"oracle {t_ref:.1f} s")
+    return g, ref, out
+
+
+def test_plan_and_marginals_10k(runs):
+    g, ref, out = runs
+    T, Tr = out["T"], np.exp(ref["logS"])
+    rel = float(np.linalg.norm(T - Tr) / np.linalg.norm(Tr))
+    m, mr = T.sum(axis=0), Tr.sum(axis=0)
+    dm = float(np.abs(m - mr).max())
+    dr = float(np.abs(T.sum(axis=1) - 1.0 / g.n1).max())
+    print(f"plan {rel:.3e}; column marginals {dm * g.n2:.3e} x 1/n2; rows {dr * g.n1:.3e} x 1/n1")
+    assert all(st == 0 and it == SINK for it, _, st in out["hist"])
+    assert rel <= 1e-4
+    assert dm <= 1e-6 / g.n2 + 1e-6 * np.abs(mr).max()
+    assert dr <= 1e-6 / g.n1
+
+
+def test_topk_and_hits_10k(runs):
+    g, ref, out = runs
+    Tr = np.exp(ref["logS"])
+    srt = -np.sort(-Tr, axis=1)[:, :11]
+    clear = ((srt[:, :10] - srt[:, 1:11]) / srt[:, :1] > 1e-5).all(axis=1)
+    want = R.topk(Tr, 10)
+    agree = np.all(out["idx"] == want, axis=1)
+    print(f"rows with clear margins {int(clear.sum())} of {g.n1}; "
+          f"identical top-10 there {int(agree[clear].sum())}")
+    assert clear.sum() > 0.5 * g.n1
+    assert np.all(agree[clear])
+    hr = R.hits_mrr(Tr, g.test_pairs)
+    assert abs(out["hits"]["hits@1"] - hr["hits@1"]) <= 1.0 / len(g.test_pairs) + 1e-12

@@ -2,9 +2,14 @@
 configuration bench.py times (default sweep shape, BF16 kernel storage, the
 learned warm start), through the C ABI.
 
-* Sampled rows of the first outer iteration's row-stabilised Gibbs kernel
-  (Phases 1-2 of Algorithm 1 from the independent coupling) against the FP64 row oracle
+* Sampled rows (the five highest-degree hubs among them) of the first
+  outer iteration's row-stabilised Gibbs kernel (Phases 1-2 of Algorithm 1
+  from the independent coupling) against the FP64 row oracle
   (oracle/rows_ref.py), FP32 and BF16 storage.
+* The same rows of an outer iteration whose previous plan is a seeded
+  general one (T_prev = diag(u) K diag(v) with K spanning e^-10 .. 1), so
+  Pass A and Pass B gather a full-rank plan, against the row oracle's
+  general-plan form.
 * Sinkhorn to 1e-4 (Eq. 3): row and column marginals recomputed
   independently in float64 from the stored K and the potentials; the
   reported error must match them and meet the tolerance.
@@ -48,7 +53,11 @@ def setup():
     rng = np.random.default_rng(5)
     rows = list(rng.choice(np.flatnonzero(deg <= 40), 6, replace=False))
     anc = [int(i) for i, _ in g.anchors if deg[int(i)] <= 40][:1]
-    rows = [int(r) for r in rows] + anc + [g.n1 - 1]
+    # the five highest-degree rows: the hubs of the heavy-tailed degree
+    # distribution, where the edge-balanced split of the sparse products
+    # spreads one row's neighbours over many warps
+    hubs = [int(i) for i in np.argsort(-deg, kind="stable")[:5]]
+    rows = [int(r) for r in rows] + anc + hubs + [g.n1 - 1]
     return g, p, st, rows
 
 
@@ -78,6 +87,56 @@ def test_first_iteration_kernel_rows_50k(setup, dtype):
     print(f"{dtype}: max |dK| {err.max():.3e}, worst / bound {worst:.3f}")
     assert worst <= 1.0
     # every row is stabilised: its largest entry is exactly 1
+    np.testing.assert_array_equal(Kg.max(axis=1), 1.0)
+
+
+@pytest.fixture(scope="module")
+def general_plan(setup):
+    """A seeded general previous plan at full size: K (bf16 grid, 5 GB as
+    bfloat16 on the host) and the log-scalings."""
+    g, p, st, rows = setup
+    ld = (g.n2 + 127) // 128 * 128
+    rng = synth.rng_for(4242)
+    K = torch.zeros((g.n1, ld), dtype=torch.bfloat16)
+    for i0 in range(0, g.n1, 2000):
+        blk = synth.random_kernel_rows(min(2000, g.n1 - i0), g.n2, rng)
+        K[i0:i0 + blk.shape[0], : g.n2] = torch.from_numpy(blk).to(torch.bfloat16)
+    lu = synth.random_log_scalings(g.n1, rng)
+    lv = synth.random_log_scalings(g.n2, rng)
+    return K, lu, lv
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_general_plan_kernel_rows_50k(setup, general_plan, dtype):
+    g, p, st, rows = setup
+    K, lu, lv = general_plan
+    al = _aligner(g, dtype)
+    try:
+        al.node_cost(g.X1, g.X2, g.anchors)
+        for i0 in range(0, g.n1, 5000):
+            al.K[i0:i0 + 5000].copy_(K[i0:i0 + 5000].to(al.device).to(al.K.dtype))
+        al.log_u.copy_(torch.from_numpy(lu))
+        al.log_v.copy_(torch.from_numpy(lv))
+        al.align_iter()
+        idx = torch.tensor(rows, device=al.device)
+        Kg = al.K.index_select(0, idx)[:, : g.n2].double().cpu().numpy()
+    finally:
+        al.close()
+    u = np.exp(lu.astype(np.float64))
+    v = np.exp(lv.astype(np.float64))
+
+    def plan_rows(ks):
+        ks = np.asarray(ks, dtype=np.int64)
+        Kk = K[torch.from_numpy(ks), : g.n2].double().numpy()
+        return u[ks, None] * Kk * v[None, :]
+
+    Kr = rows_ref.kernel_rows_from_plan(st, g.anchors, p, rows, plan_rows,
+                                        "f64" if dtype == "f32" else "bf16")
+    rel = 5e-4 if dtype == "f32" else 5e-3
+    err = np.abs(Kg - Kr)
+    worst = float((err / (rel * Kr + 1e-6)).max())
+    print(f"{dtype}: max |dK| {err.max():.3e}, worst / bound {worst:.3f}")
+    assert worst <= 1.0
     np.testing.assert_array_equal(Kg.max(axis=1), 1.0)
 
 

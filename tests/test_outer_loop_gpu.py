@@ -98,25 +98,40 @@ def test_convergence_driven_outer_loop(small):
         assert abs(got - want) <= 1e-3 * want + 1e-6, (k, got, want)
 
 
-def test_checkpoint_resume_reproduces_the_run(small, tmp_path):
+@pytest.mark.parametrize("mode", ["cold", "prev", "learned"])
+def test_checkpoint_resume_reproduces_the_run(small, tmp_path, mode):
+    """A run interrupted after 2 of 4 outer iterations and resumed from its
+    checkpoint ends with the uninterrupted run's plan, bit for bit, with
+    the cold start and with both warm starts (whose carried correction is
+    part of the checkpoint)."""
+    from paper_2607_11952_gb300 import gnn
     g = small
     path = str(tmp_path / "align.ckpt")
+    model = gnn.WarmStartModel.load(gnn.WEIGHTS_PATH) if mode == "learned" else None
+
+    def starter(al):
+        return None if mode == "cold" else gnn.WarmStarter(al, mode, model)
+
     a = _aligner(g, "bf16")
     try:
-        a.align(g.X1, g.X2, g.anchors, n_outer=2, n_sink=20, checkpoint=path)
+        a.align(g.X1, g.X2, g.anchors, n_outer=2, n_sink=20, tol=1e-6, check_every=5,
+                warm=starter(a), checkpoint=path)
     finally:
         a.close()
     b = _aligner(g, "bf16")
     try:
-        hist = b.align(g.X1, g.X2, g.anchors, n_outer=4, n_sink=20, resume=path)
+        hist = b.align(g.X1, g.X2, g.anchors, n_outer=4, n_sink=20, tol=1e-6,
+                       check_every=5, warm=starter(b), resume=path)
         Tb = b.plan_f64()
     finally:
         b.close()
     c = _aligner(g, "bf16")
     try:
-        c.align(g.X1, g.X2, g.anchors, n_outer=4, n_sink=20)
+        hc = c.align(g.X1, g.X2, g.anchors, n_outer=4, n_sink=20, tol=1e-6,
+                     check_every=5, warm=starter(c))
         Tc = c.plan_f64()
     finally:
         c.close()
     assert len(hist) == 2
+    assert [h[0] for h in hist] == [h[0] for h in hc[2:]]
     np.testing.assert_array_equal(Tb, Tc)

@@ -1,0 +1,78 @@
+"""The fused Sinkhorn sweep (Algorithm 1, Phase 3; Eq. 3) in the launch
+shape of the 50k workload, against the FP64 oracle's scaling-domain
+iteration on the same kernel.
+
+The row width is the workload's (n2 = 50,000 columns, ld = 50,048), so the
+planner picks the shape bench.py times (the cluster size, column slab,
+vectors per thread and the slab's ragged last vector round depend on ld,
+not on n1); 2,000 rows keep the FP64 oracle quick.  K is a seeded general
+kernel (entries spanning e^-10 .. 1, on the bfloat16 grid so FP32 and BF16
+storage hold the same values), the start v0 a seeded column scaling.  Ten
+iterations from v0: u = mu / (K v), v = nu / (K^T u).
+
+Tolerance: the device sums each row and column in FP32 (products of exact
+bf16 values with FP32 scalings): a relative error of a few 1e-6 per
+iteration, which ten iterations of the contraction do not amplify
+past 1e-4 -- the plan tolerance of the FP32 path (||dT||_F/||T||_F
+<= 1e-4) applied to u and v themselves."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fastalign_ref as R  # noqa: E402
+from paper_2607_11952_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+N1, N2, ITERS = 2000, 50_000, 10
+
+
+@pytest.fixture(scope="module")
+def case():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    rng = synth.rng_for(2024)
+    K = synth.random_kernel_rows(N1, N2, rng)
+    lv0 = synth.random_log_scalings(N2, rng)
+    mu, nu = np.full(N1, 1.0 / N1), np.full(N2, 1.0 / N2)
+    u, v, _ = R.sinkhorn_scaling(K.astype(np.float64), mu, nu, ITERS,
+                                 v0=np.exp(lv0.astype(np.float64)), track_err=False)
+    return K, lv0, u, v
+
+
+def _run(K, lv0, dtype):
+    from paper_2607_11952_gb300 import api
+    empty = np.zeros((0, 2), np.int64)
+    al = api.Aligner(api.Graph(N1, empty), api.Graph(N2, empty), api.Params(dtype=dtype))
+    try:
+        kt = torch.from_numpy(K).to(al.device)
+        al.K.zero_()
+        al.K[:, :N2].copy_(kt.to(al.K.dtype))
+        al.log_v.copy_(torch.from_numpy(lv0))
+        it, err, st = al.sinkhorn(ITERS)
+        torch.cuda.synchronize()
+        return (al.log_u.double().cpu().numpy(), al.log_v.double().cpu().numpy(),
+                it, st, al.ld)
+    finally:
+        al.close()
+
+
+@pytest.mark.parametrize("q", [0, 16])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_workload_sweep_shape_matches_oracle(case, monkeypatch, dtype, q):
+    """q = 0: the planner's own shape for this width (the bench's);
+    q = 16: the largest cluster."""
+    from paper_2607_11952_gb300 import _lib as L
+    K, lv0, u, v = case
+    if q:
+        monkeypatch.setenv("FA_SWEEP_Q", str(q))
+    plan = L.fa_sweep_plan(N1, 50_048, L.FA_BF16 if dtype == "bf16" else L.FA_F32)
+    lu, lv, it, st, ld = _run(K, lv0, dtype)
+    assert ld == 50_048 and it == ITERS and st == 0
+    du = np.abs(lu - np.log(u)).max()
+    dv = np.abs(lv - np.log(v)).max()
+    print(f"{dtype} plan {plan}: max |d log u| {du:.2e}, max |d log v| {dv:.2e}")
+    assert du <= 1e-4 and dv <= 1e-4
