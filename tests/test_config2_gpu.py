@@ -9,8 +9,8 @@ Tolerances (the FP32 path's, written here):
 * column marginals: |m - m_ref|_inf <= 1e-6 / n2 + 1e-6 max m_ref (1e-6
   relative to 1/n); row marginals within 1e-6 / n1 of mu (rows are exact
   after the b update up to FP32 rounding of the row sums);
-* top-10 indices identical in every row whose relative score gaps
-  (T_(k) - T_(k+1)) / T_(1), k = 1..10, all exceed 1e-5;
+* top-10: every position whose value is separated from both neighbours in
+  the sorted row by more than 1e-5 T_(1) holds the oracle's column;
 * Hits@1 within one test pair of the oracle's."""
 import time
 
@@ -71,12 +71,16 @@ def test_topk_and_hits_10k(runs):
     g, ref, out = runs
     Tr = np.exp(ref["logS"])
     srt = -np.sort(-Tr, axis=1)[:, :11]
-    clear = ((srt[:, :10] - srt[:, 1:11]) / srt[:, :1] > 1e-5).all(axis=1)
+    gap = (srt[:, :10] - srt[:, 1:11]) / srt[:, :1] > 1e-5     # gap after position k
+    # position k holds a unique column when it is separated from both
+    # neighbours (position 0 only from the next)
+    before = np.concatenate([np.ones((g.n1, 1), bool), gap[:, :9]], axis=1)
+    fixed = gap & before
     want = R.topk(Tr, 10)
-    agree = np.all(out["idx"] == want, axis=1)
-    print(f"rows with clear margins {int(clear.sum())} of {g.n1}; "
-          f"identical top-10 there {int(agree[clear].sum())}")
-    assert clear.sum() > 0.5 * g.n1
-    assert np.all(agree[clear])
+    same = out["idx"] == want
+    print(f"determined positions {int(fixed.sum())} of {fixed.size}; top-1 determined in "
+          f"{int(fixed[:, 0].sum())} rows; mismatches there {int((fixed & ~same).sum())}")
+    assert fixed[:, 0].sum() > 0.9 * g.n1
+    assert np.all(same[fixed])
     hr = R.hits_mrr(Tr, g.test_pairs)
     assert abs(out["hits"]["hits@1"] - hr["hits@1"]) <= 1.0 / len(g.test_pairs) + 1e-12
