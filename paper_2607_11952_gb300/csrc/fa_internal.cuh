@@ -138,8 +138,10 @@ struct SweepPlan {
   int NS = 2;        // shared-memory ring stages
   int NT = 512;      // threads per CTA (256: two CTAs per SM)
   int G = 1;         // clusters (= rows of the partial column-sum buffer)
-  int kind = 0;      // 0: CTA-synchronous sweep, 1: warp-specialised sweep
+  int kind = 0;      // 0: CTA-synchronous sweep, 1: warp-specialised sweep,
+                     // 2: tensor-core row pass (BF16 storage only)
   int L = 1;         // warp-specialised: steps the column pass lags the row pass
+  int MB = 1;        // tensor-core sweep: CTAs per SM its shape is sized for
 };
 SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G);
 fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,

@@ -27,6 +27,8 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "fa_internal.cuh"
 #include "sweep_dev.cuh"
 
@@ -539,10 +541,76 @@ static SweepPlan plan_sweep_ws(int64_t ld, bool bf16) {
   return sp;
 }
 
+// tensor-core row-pass sweep (k_sweep_mma.cu)
+void* sweep_mma_kernel(int S, int NW, int MINB);
+size_t sweep_mma_smem(int NS, int R, int W, int NW);
+
+// Shape of the tensor-core sweep: two stages of R rows (R <= 8; the MMA
+// tile holds 8) per CTA, two 128-thread CTAs per SM when they fit, else one
+// 256-thread CTA.  Larger R first (fewer steps, less per-step overhead),
+// then the smaller cluster.  FA_SWEEP_MB / FA_SWEEP_Q / FA_SWEEP_R force
+// the CTAs per SM, the cluster size and the rows per step (tuning).
+static SweepPlan plan_sweep_mma(int64_t ld) {
+  SweepPlan sp;
+  sp.Q = 0;
+  sp.kind = 2;
+  const int MBforce = env_int("FA_SWEEP_MB", 0);
+  const int Qforce = env_int("FA_SWEEP_Q", 0);
+  const int Rforce = env_int("FA_SWEEP_R", 0);
+  const size_t sm_bytes = 228 * 1024, reserved = 1024, cta_max = 227 * 1024;
+  for (int MB = 2; MB >= 1 && sp.Q == 0; --MB) {
+    if (MBforce && MB != MBforce) continue;
+    const int NW = MB == 2 ? 4 : 8;
+    const int smax = MB == 2 ? 6 : 8;         // instantiated register shapes
+    const size_t budget = std::min(cta_max, sm_bytes / MB - reserved);
+    const int rmin = MB == 2 ? 6 : 4;
+    for (int R = 8; R >= rmin && sp.Q == 0; --R) {
+      if (Rforce && R != Rforce) continue;
+      for (int Q = 1; Q <= kMaxQ; Q *= 2) {
+        if (Qforce && Q != Qforce) continue;
+        if (ld % Q) continue;
+        const int64_t W = ld / Q;
+        if (W % 8) continue;
+        const int64_t vecs = W / 8;
+        const int S = (int)((vecs + NW * 32 - 1) / (NW * 32));
+        if (S > smax) continue;
+        if (sweep_mma_smem(2, R, (int)W, NW) > budget) continue;
+        sp.Q = Q;
+        sp.W = (int)W;
+        sp.S = S;
+        sp.R = R;
+        sp.NS = 2;
+        sp.NT = NW * 32;
+        sp.MB = MB;
+        break;
+      }
+    }
+  }
+  return sp;
+}
+
 SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   SweepPlan sp;
   sp.Q = 0;
-  if (env_int("FA_SWEEP_KIND", 0) != 0) {
+  // BF16 storage: the tensor-core row pass unless FA_SWEEP_KIND selects
+  // another sweep (0: CTA-synchronous, 1: warp-specialised)
+  const int kind_env = env_int("FA_SWEEP_KIND", bf16 ? 2 : 0);
+  if (bf16 && kind_env == 2) {
+    sp = plan_sweep_mma(ld);
+    if (sp.Q > 0) {
+      int G = env_int("FA_SWEEP_G", 0);
+      if (G <= 0) G = max_G;
+      const int steps = (n1 + sp.R - 1) / sp.R;
+      if (G > steps) G = steps;
+      if (G > max_G) G = max_G;
+      if (G < 1) G = 1;
+      sp.G = G;
+      return sp;
+    }
+    sp = SweepPlan();   // no tensor-core shape: fall back below
+    sp.Q = 0;
+  }
+  if (kind_env == 1) {
     sp = plan_sweep_ws(ld, bf16);
     if (sp.Q > 0) {
       int G = env_int("FA_SWEEP_G", 0);
@@ -612,9 +680,11 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
 }
 
 static size_t sweep_dyn_smem(const SweepPlan& sp, bool bf16) {
+  if (sp.kind == 2) return sweep_mma_smem(sp.NS, sp.R, sp.W, sp.NT / 32);
   return sp.kind ? sweep_ws_smem(sp.NS, sp.R, sp.W, bf16) : sweep_smem(sp, bf16);
 }
 static void* sweep_fn(const SweepPlan& sp, bool bf16) {
+  if (sp.kind == 2) return bf16 ? sweep_mma_kernel(sp.S, sp.NT / 32, sp.MB) : nullptr;
   return sp.kind ? sweep_ws_kernel(bf16, sp.S, sp.R) : sweep_kernel(bf16, sp.S, sp.R, sp.NT);
 }
 
@@ -622,7 +692,7 @@ static cudaLaunchConfig_t sweep_config(const SweepPlan& sp, bool bf16, unsigned 
                                        cudaLaunchAttribute* attr, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3((unsigned)(sp.kind ? sweep_ws_threads() : sp.NT));
+  cfg.blockDim = dim3((unsigned)(sp.kind == 1 ? sweep_ws_threads() : sp.NT));
   cfg.dynamicSmemBytes = sweep_dyn_smem(sp, bf16);
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -670,13 +740,19 @@ fa_status launch_sweep(const SweepPlan& sp, int n1, int n2, int64_t ld,
   void* args_ws[] = {(void*)&K, (void*)&ld, (void*)&n1, (void*)&n2, (void*)&W,
                      (void*)&NS, (void*)&L, (void*)&log_v, (void*)&log_u, (void*)&mu,
                      (void*)&log_mu, (void*)&colpart, (void*)&status};
-  e = cudaLaunchKernelExC(&cfg, fn, sp.kind ? args_ws : args);
+  int R = sp.R;
+  void* args_mma[] = {(void*)&K, (void*)&ld, (void*)&n1, (void*)&n2, (void*)&W,
+                      (void*)&NS, (void*)&R, (void*)&log_v, (void*)&log_u, (void*)&mu,
+                      (void*)&log_mu, (void*)&colpart, (void*)&status};
+  e = cudaLaunchKernelExC(&cfg, fn, sp.kind == 2 ? args_mma : sp.kind ? args_ws : args);
   if (e != cudaSuccess) {
-    set_error("k_sweep launch (Q=%d S=%d R=%d NS=%d G=%d): %s", sp.Q, sp.S, sp.R,
-              sp.NS, sp.G, cudaGetErrorString(e));
+    set_error("k_sweep launch (kind=%d Q=%d S=%d R=%d NS=%d G=%d): %s", sp.kind, sp.Q, sp.S,
+              sp.R, sp.NS, sp.G, cudaGetErrorString(e));
     return FA_ERR_CUDA;
   }
-  if (sp.kind) FA_LAUNCHED("k_sweep_ws"); else FA_LAUNCHED("k_sweep");
+  if (sp.kind == 2) FA_LAUNCHED("k_sweep_mma");
+  else if (sp.kind) FA_LAUNCHED("k_sweep_ws");
+  else FA_LAUNCHED("k_sweep");
   return FA_OK;
 }
 

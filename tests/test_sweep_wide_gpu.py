@@ -76,3 +76,55 @@ def test_workload_sweep_shape_matches_oracle(case, monkeypatch, dtype, q):
     dv = np.abs(lv - np.log(v)).max()
     print(f"{dtype} plan {plan}: max |d log u| {du:.2e}, max |d log v| {dv:.2e}")
     assert du <= 1e-4 and dv <= 1e-4
+
+
+# every tensor-core sweep shape on a ragged kernel: 1003 rows (a partial
+# last step for every R), 4700 columns (ld 4736: a partial last column pair
+# and padding columns in the last slab)
+M1, M2 = 1003, 4700
+MMA_SHAPES = ([{"FA_SWEEP_MB": mb, "FA_SWEEP_Q": q} for mb in (1, 2) for q in (1, 2, 4, 8, 16)]
+              + [{"FA_SWEEP_MB": 2, "FA_SWEEP_Q": 4, "FA_SWEEP_R": r} for r in (6, 7)]
+              + [{"FA_SWEEP_MB": 1, "FA_SWEEP_Q": 2, "FA_SWEEP_R": r} for r in (4, 5)])
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    rng = synth.rng_for(2025)
+    K = synth.random_kernel_rows(M1, M2, rng)
+    lv0 = synth.random_log_scalings(M2, rng)
+    mu, nu = np.full(M1, 1.0 / M1), np.full(M2, 1.0 / M2)
+    u, v, _ = R.sinkhorn_scaling(K.astype(np.float64), mu, nu, ITERS,
+                                 v0=np.exp(lv0.astype(np.float64)), track_err=False)
+    return K, lv0, u, v
+
+
+@pytest.mark.parametrize("env", MMA_SHAPES,
+                         ids=["-".join(f"{k[9:]}{v}" for k, v in e.items()) for e in MMA_SHAPES])
+def test_tensor_core_sweep_shapes_match_oracle(ragged, monkeypatch, env):
+    from paper_2607_11952_gb300 import _lib as L
+    from paper_2607_11952_gb300 import api
+    K, lv0, u, v = ragged
+    for k, val in env.items():
+        monkeypatch.setenv(k, str(val))
+    plan = L.fa_sweep_plan(M1, 4736, L.FA_BF16)
+    assert plan["kind"] == 2 and plan["Q"] == env["FA_SWEEP_Q"], plan
+    empty = np.zeros((0, 2), np.int64)
+    al = api.Aligner(api.Graph(M1, empty), api.Graph(M2, empty), api.Params(dtype="bf16"))
+    try:
+        al.K.zero_()
+        al.K[:, :M2].copy_(torch.from_numpy(K).to(al.device).to(al.K.dtype))
+        al.log_v.copy_(torch.from_numpy(lv0))
+        it, err, st = al.sinkhorn(ITERS)
+        torch.cuda.synchronize()
+        lu, lv = al.log_u.double().cpu().numpy(), al.log_v.double().cpu().numpy()
+    finally:
+        al.close()
+    du = np.abs(lu - np.log(u)).max()
+    dv = np.abs(lv - np.log(v)).max()
+    print(f"plan {plan}: max |d log u| {du:.2e}, max |d log v| {dv:.2e}")
+    assert it == ITERS and st == 0
+    assert du <= 1e-4 and dv <= 1e-4
