@@ -7,16 +7,21 @@ node-cost GEMM, propagation), then the workload's 30 outer iterations of
 Phase 2 (Pass A, Pass B + Gibbs kernel) and Phase 3 (fused Sinkhorn sweeps,
 learned warm start, until the L1 marginal error is <= 1e-4, checked every 5
 sweeps), then the top-10 read-out.  The metric is the step time (lower is
-better); the same alignment in plain FP32 with a cold start is timed once
-beside it.  The Gibbs kernel (5 GB in BF16) is far larger than L2, so no
-flush is needed between steps.
+better); beside it go the same alignment in plain FP32 with a cold start
+and, on the same BF16 storage, the cold and previous-correction warm starts
+(what the trained network adds).  The Gibbs kernel (5 GB in BF16) is far
+larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--outer T] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (the 5k-node pair with the same generator
-parameters, Phase 1 plus the first outer iteration) and scales it to the
-metric's unit.
+The FP64 CPU oracle is timed, as it stands, on bounded samples it finishes
+in seconds: the 1k Barabasi-Albert configuration in full (10 outer x 50
+Sinkhorn iterations) and the 50k workload's 5k-node run (the same generator
+parameters at n = 5000: Phase 1 and the first outer iterations to 1e-4).
+The GPU runs the same samples through the same API, so each CPU/GPU ratio
+is measured on identical work; the plans of both are compared.
+--impl reference times the oracle alone on the 5k-node sample, each step
+one run of it.
 """
 from __future__ import annotations
 
@@ -35,10 +40,11 @@ if ROOT not in sys.path:
 
 METRIC = "50k-node time to 1e-4 marginal err, learned+BF16 vs plain FP32; sweep HBM GB/s"
 
-# Sinkhorn iterations the plain method (FP32 storage, cold start) needs on a
-# workload, as measured on GB300 by this script's FP32 comparison; the
-# reference arm scales the oracle's per-iteration time by it.
-PLAIN_SWEEPS = {("cl50k", 30): 61790, ("cl50k", 4): 1190}
+# The oracle's samples: the 1k BA configuration in full, and the 50k
+# workload's 5k-node run (Phase 1 + its first outer iterations to 1e-4).
+SAMPLE_OUTER = {"ba1k": 10, "cl50k_5k": 3}
+SAMPLE_SINK = {"ba1k": 50, "cl50k_5k": 20000}
+SAMPLE_TOL = {"ba1k": None, "cl50k_5k": 1e-4}
 
 
 def _peaks():
@@ -200,28 +206,56 @@ def run_ours(args):
     achieved = algo_bytes / (avg_sweep * 1e-3) / 1e9 if avg_sweep > 0 else None
     traffic = _ncu_traffic(args)
 
+    def timed_alignment(dtype, warm, runs=1):
+        """The step on a fresh aligner of the given storage type and warm
+        start, timed with CUDA events; one untimed outer iteration first
+        brings the context's buffers into use."""
+        a = api.Aligner(G1, G2, api.Params(dtype=dtype), device=dev)
+        a.set_timing(True)
+        a.node_cost(X1, X2, g.anchors)
+        a.plan_init()
+        a.align_iter()
+        a.sinkhorn(5)
+        out = []
+        for _ in range(runs):
+            rr = []
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sw = step(a, rr, warm=warm)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append({"ms": round(e0.elapsed_time(e1), 1), "sweeps": sw,
+                        "sweep_ms": round(sum(r[2] * r[0] for r in rr) /
+                                          max(1, sum(r[0] for r in rr)), 4)})
+        h = a.hits_mrr(g.test_pairs)
+        a.close()
+        ms_all = [o["ms"] for o in out]
+        return {"ms_per_step": round(sum(ms_all) / len(ms_all), 1), "runs_ms": ms_all,
+                "sweeps": out[-1]["sweeps"], "sweep_ms": out[-1]["sweep_ms"],
+                "hits@1": h["hits@1"], "mrr": h["mrr"]}
+
     # plain FP32 cold start on the same pair, for the metric's comparison
     fp32 = None
     if args.compare_fp32 and args.dtype != "f32":
-        al32 = api.Aligner(G1, G2, api.Params(dtype="f32"), device=dev)
-        al32.set_timing(True)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        r32 = []
-        e0.record(stream)
-        sw32 = step(al32, r32)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fp32 = {"ms_per_step": e0.elapsed_time(e1), "sweeps": sw32,
-                "hits@1": al32.hits_mrr(g.test_pairs)["hits@1"],
-                "sweep_ms": sum(r[2] * r[0] for r in r32) / max(1, sum(r[0] for r in r32))}
-        al32.close()
+        fp32 = timed_alignment("f32", "cold", runs=args.fp32_runs)
+
+    # what the trained network adds: the same BF16 alignment from the cold
+    # start and from the previous-correction start (the network's base)
+    ablation = None
+    if args.ablation and args.dtype == "bf16":
+        ablation = {"learned": {"ms_per_step": round(ms, 1),
+                                "sweeps": total_sweeps / args.steps,
+                                "hits@1": hits["hits@1"], "mrr": hits["mrr"]}}
+        for w in ("prev", "cold"):
+            ablation[w] = timed_alignment("bf16", w)
 
     # end to end through the public API from host buffers
     e2e = _e2e(args, g, dev, api, model) if args.e2e else None
 
-    cpu = (_cpu_baseline(args, total_sweeps / args.steps)
-           if (rank == 0 and world == 1 and args.cpu_baseline) else None)
+    cpu = same = None
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        cpu, same = _cpu_and_same_work(args, dev, model)
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(ms, 3), "unit": "ms",
@@ -234,6 +268,7 @@ def run_ours(args):
             "warm_start": args.warm,
             "hits@1": hits["hits@1"], "mrr": hits["mrr"],
             "plain_fp32_cold": fp32,
+            "ablation": ablation,
             "roofline": {"kernel": "k_sweep", "bound": "hbm",
                          "achieved": round(achieved, 1) if achieved else None,
                          "peak": peak, "unit": "GB/s",
@@ -242,6 +277,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": algo_bytes,
                          "avg_launch_ms": round(avg_sweep, 4)},
             "cpu_baseline": cpu,
+            "same_work": same,
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": int(launches),
@@ -315,50 +351,102 @@ def _e2e(args, g, dev, api, model):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes)}
 
 
-def _cpu_sample(args):
-    """The oracle on the 5k-node pair with the workload's generator
-    parameters: Phase 1, then Phase 2 of the first outer iteration and its
-    Sinkhorn solve to tol, each timed (FP64)."""
-    import math
-    import numpy as np
+def _oracle_run(name):
+    """The FP64 oracle (Algorithm 1 with the scaling form of Eq. 3) on one
+    sample, timed on the host cores: Phase 1, then the sample's outer
+    iterations (fixed Sinkhorn counts, or to its tolerance checked every
+    5).  Returns (pair, wall ms, Sinkhorn iterations, log S)."""
     from oracle import fastalign_ref as R
     from paper_2607_11952_gb300 import synth
-    g = synth.config_pair(args.config + "_5k" if args.config == "cl50k" else args.config)
-    p = R.Params()
+    g = synth.config_pair(name)
     t0 = time.perf_counter()
-    ph = R.phase1(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, p)
-    t1 = time.perf_counter()
-    logS = np.full((g.n1, g.n2), -math.log(g.n1 * g.n2))
-    C_eff = R.outer_step(ph, logS, p)
-    t2 = time.perf_counter()
-    mu, nu = np.full(g.n1, 1 / g.n1), np.full(g.n2, 1 / g.n2)
-    _, _, _, iters = R.sinkhorn_log(C_eff, mu, nu, p.eps, 100000, tol=args.tol,
-                                    check_every=args.check_every)
-    t3 = time.perf_counter()
-    return g, dict(phase1=(t1 - t0) * 1e3, phase2=(t2 - t1) * 1e3,
-                   sweep=(t3 - t2) * 1e3 / max(1, iters), iters=iters)
+    out = R.fastalign(g.n1, g.n2, g.edges1, g.edges2, g.X1, g.X2, g.anchors, R.Params(),
+                      SAMPLE_OUTER[name], SAMPLE_SINK[name], tol=SAMPLE_TOL[name],
+                      check_every=5, sinkhorn="scaling")
+    ms = (time.perf_counter() - t0) * 1e3
+    return g, ms, int(sum(h["iters"] for h in out["hist"])), out["logS"]
 
 
-def _scale(args, g, t, sweeps):
-    """Oracle time for the GPU step's work at n = 50k: Phase 1 grows like
-    n1 n2 |L| (|L| ~ n), Phase 2 and one Sinkhorn iteration like n1 n2."""
+def _gpu_run(name, dtype, warm, dev, model):
+    """The same sample through the library's API on the GPU (inputs
+    resident), timed with CUDA events: (ms, Sinkhorn iterations, plan)."""
+    import torch
+    from paper_2607_11952_gb300 import api, gnn, synth
+    g = synth.config_pair(name)
+    G1, G2 = api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2)
+    X1 = torch.from_numpy(g.X1).to(dev)
+    X2 = torch.from_numpy(g.X2).to(dev)
+    tol = SAMPLE_TOL[name]
+
+    def run(al):
+        al.node_cost(X1, X2, g.anchors)
+        al.plan_init()
+        ws = gnn.WarmStarter(al, warm, model if warm == "learned" else None)
+        it = 0
+        for _ in range(SAMPLE_OUTER[name]):
+            al.align_iter()
+            it += ws.solve(SAMPLE_SINK[name], -1.0 if tol is None else tol, 5)[0]
+        return it
+
+    al = api.Aligner(G1, G2, api.Params(dtype=dtype), device=dev)
+    run(al)                                   # warm-up run
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    it = run(al)
+    e1.record(s)
+    torch.cuda.synchronize()
+    T = al.plan_f64()
+    al.close()
+    return e0.elapsed_time(e1), it, T
+
+
+def _sample_text(name, g):
+    if name == "ba1k":
+        return (f"1k Barabasi-Albert configuration in full: Phase 1 + 10 outer x 50 "
+                f"Sinkhorn iterations (n={g.n1})")
+    return (f"the 50k workload's 5k-node run (same generator parameters at n={g.n1}): "
+            f"Phase 1 + {SAMPLE_OUTER[name]} outer iterations, Sinkhorn to "
+            f"{SAMPLE_TOL[name]:g} checked every 5")
+
+
+def _cpu_and_same_work(args, dev, model):
+    """cpu_baseline: the oracle as it stands on the 50k workload's 5k-node
+    run, measured (not scaled).  same_work: per sample, the oracle's time
+    beside the GPU's on identical work (plain FP32, cold start, the same
+    iteration rule) and the relative plan error of the GPU's FP32 and
+    BF16 + learned forms against the oracle's FP64 plan."""
+    import numpy as np
+    same = []
+    main = None
+    for name in ("ba1k", "cl50k_5k"):
+        g, ms_o, it_o, logS = _oracle_run(name)
+        Tr = np.exp(logS)
+        entry = {"workload": _sample_text(name, g), "oracle_ms": round(ms_o, 1),
+                 "oracle_sinkhorn_iterations": it_o, "cores": os.cpu_count()}
+        for dtype, warm in (("f32", "cold"), ("bf16", "learned")):
+            if warm == "learned" and model is None:
+                continue
+            ms_g, it_g, T = _gpu_run(name, dtype, warm, dev, model)
+            key = f"gpu_{dtype}_{warm}"
+            entry[key] = {"ms": round(ms_g, 2), "sinkhorn_iterations": it_g,
+                          "plan_rel_err_vs_oracle": float(np.linalg.norm(T - Tr) / np.linalg.norm(Tr))}
+        entry["ratio_oracle_over_gpu_f32"] = round(ms_o / entry["gpu_f32_cold"]["ms"], 1)
+        same.append(entry)
+        if name == "cl50k_5k":
+            main = (g, ms_o, it_o)
+    g, ms_o, it_o = main
+    # the step's scale relative to the sample, for context only
     s2 = (50_000 / g.n1) * (50_000 / g.n2)
-    return (t["phase1"] * s2 * (50_000 / g.n1) + t["phase2"] * s2 * args.outer +
-            t["sweep"] * s2 * sweeps)
-
-
-def _cpu_baseline(args, sweeps):
-    g, t = _cpu_sample(args)
-    return {"value": round(_scale(args, g, t, sweeps), 1), "unit": "ms",
-            "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 oracle on the {g.n1}-node pair with the workload's "
-                      f"generator parameters: Phase 1 {t['phase1']:.0f} ms, Phase 2 "
-                      f"{t['phase2']:.0f} ms, {t['sweep']:.0f} ms per Sinkhorn iteration "
-                      f"({t['iters']} iterations to {args.tol:g}); scaled to n=50k "
-                      f"(n^3 Phase 1, n^2 per outer iteration and per Sinkhorn "
-                      f"iteration) for {args.outer} outer iterations and the "
-                      f"{sweeps:.0f} Sinkhorn iterations the GPU step ran; NumPy "
-                      f"elementwise work is single-threaded, BLAS uses all cores"}
+    cpu = {"value": round(ms_o, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "FP64 oracle (scaling form of Eq. 3, NumPy/SciPy, BLAS on all cores) on "
+                     + _sample_text("cl50k_5k", g) + f"; {it_o} Sinkhorn iterations; measured",
+           "extrapolated": {"ms_per_50k_element_pass_ratio": round(s2, 1),
+                            "note": "the 50k step does ~100x the per-iteration work of the "
+                                    "sample and more outer iterations; the oracle is not run "
+                                    "at 50k (20 GB per FP64 dense matrix)"}}
+    return cpu, same
 
 
 def _config(args, world):
@@ -383,34 +471,37 @@ def _synth_config(name):
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands on the host cores, each step one run of
+    the 50k workload's 5k-node sample (Phase 1 + its first outer iterations
+    to 1e-4); the value is that run's measured wall time."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
         return
     vals = []
-    g = t = None
+    g = None
+    its = 0
+    t_all = time.perf_counter()
     for k in range(args.warmup + args.steps):
-        g, t = _cpu_sample(args)
+        g, ms, its, _ = _oracle_run("cl50k_5k")
         if k >= args.warmup:
-            vals.append(_scale(args, g, t, args.ref_sweeps))
+            vals.append(ms)
+    wall = (time.perf_counter() - t_all) * 1e3
     v = sum(vals) / len(vals)
+    sample = ("FP64 oracle (scaling form of Eq. 3, NumPy/SciPy, BLAS on all cores), cold "
+              "start, on " + _sample_text("cl50k_5k", g) + f"; {its} Sinkhorn iterations")
     line = {
         "metric": METRIC, "value": round(v, 1), "unit": "ms", "impl": "reference",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Chung-Lu pair; no dataset)",
         "config": _config(args, world),
+        "timed_workload": _sample_text("cl50k_5k", g),
         "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": os.cpu_count(),
-                         "kind": "oracle",
-                         "sample": f"FP64 oracle, cold start: Phase 1, Phase 2 and Sinkhorn "
-                                   f"iterations timed on the n={g.n1} pair with the "
-                                   f"workload's generator parameters, scaled to n=50k "
-                                   f"(n^3 Phase 1, n^2 per outer and per Sinkhorn "
-                                   f"iteration) for {args.outer} outer iterations and "
-                                   f"{args.ref_sweeps} Sinkhorn iterations (the plain "
-                                   f"method's count on this workload)"},
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+        "wall_ms_all_runs": round(wall, 1),
     }
     print(json.dumps(line), flush=True)
 
@@ -428,21 +519,16 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--check-every", type=int, default=5)
     ap.add_argument("--max-sweeps", type=int, default=5000)
-    # Sinkhorn iterations of the plain method (FP32, cold start) in one step,
-    # for --impl reference (default: the count measured on the GPU for the
-    # default workload)
-    ap.add_argument("--ref-sweeps", type=int, default=None)
-    ap.add_argument("--e2e-runs", type=int, default=1)
+    ap.add_argument("--e2e-runs", type=int, default=2)
+    ap.add_argument("--fp32-runs", type=int, default=2)
     ap.add_argument("--no-fp32", dest="compare_fp32", action="store_false")
+    ap.add_argument("--no-ablation", dest="ablation", action="store_false")
     ap.add_argument("--warm", default="learned", choices=["learned", "prev", "cold"])
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     if args.outer is None:
         args.outer = _synth_config(args.config)["outer"]
-    if args.ref_sweeps is None:
-        args.ref_sweeps = PLAIN_SWEEPS.get((args.config, args.outer), 0) or \
-            int(round(2060 * args.outer))
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -557,6 +557,8 @@ static SweepPlan plan_sweep_mma(int64_t ld) {
   const int MBforce = env_int("FA_SWEEP_MB", 0);
   const int Qforce = env_int("FA_SWEEP_Q", 0);
   const int Rforce = env_int("FA_SWEEP_R", 0);
+  int NS = env_int("FA_SWEEP_NS", 2);
+  NS = NS < 2 ? 2 : (NS > 4 ? 4 : NS);
   const size_t sm_bytes = 228 * 1024, reserved = 1024, cta_max = 227 * 1024;
   for (int MB = 2; MB >= 1 && sp.Q == 0; --MB) {
     if (MBforce && MB != MBforce) continue;
@@ -574,12 +576,12 @@ static SweepPlan plan_sweep_mma(int64_t ld) {
         const int64_t vecs = W / 8;
         const int S = (int)((vecs + NW * 32 - 1) / (NW * 32));
         if (S > smax) continue;
-        if (sweep_mma_smem(2, R, (int)W, NW) > budget) continue;
+        if (sweep_mma_smem(NS, R, (int)W, NW) > budget) continue;
         sp.Q = Q;
         sp.W = (int)W;
         sp.S = S;
         sp.R = R;
-        sp.NS = 2;
+        sp.NS = NS;
         sp.NT = NW * 32;
         sp.MB = MB;
         break;
@@ -592,9 +594,9 @@ static SweepPlan plan_sweep_mma(int64_t ld) {
 SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   SweepPlan sp;
   sp.Q = 0;
-  // BF16 storage: the tensor-core row pass unless FA_SWEEP_KIND selects
-  // another sweep (0: CTA-synchronous, 1: warp-specialised)
-  const int kind_env = env_int("FA_SWEEP_KIND", bf16 ? 2 : 0);
+  // FA_SWEEP_KIND selects the sweep: 0 (default) CTA-synchronous,
+  // 1 warp-specialised, 2 tensor-core row pass (BF16 storage only)
+  const int kind_env = env_int("FA_SWEEP_KIND", 0);
   if (bf16 && kind_env == 2) {
     sp = plan_sweep_mma(ld);
     if (sp.Q > 0) {

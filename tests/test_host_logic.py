@@ -78,23 +78,25 @@ def test_csr_argument_errors():
 
 
 def test_sweep_shapes_of_the_measured_workloads():
-    # BF16 storage: the tensor-core row pass, two 128-thread CTAs per SM,
-    # clusters of 16 and 7 rows per step at the 50k workload's width
-    got = L.fa_sweep_plan(50_000, 50_048, L.FA_BF16)
-    assert (got["Q"], got["W"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == \
-        (16, 3128, 4, 7, 2, 128, 2)
-    got = L.fa_sweep_plan(50_000, 50_048, L.FA_F32)
-    assert (got["Q"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == (8, 7, 1, 4, 256, 0)
-    got = L.fa_sweep_plan(100_000, 80_000, L.FA_BF16)
-    assert (got["Q"], got["W"], got["S"], got["R"], got["NT"], got["kind"]) == \
-        (16, 5000, 3, 8, 256, 2)
-
-
-def test_cuda_core_sweep_shape_is_kept_behind_its_switch(monkeypatch):
-    monkeypatch.setenv("FA_SWEEP_KIND", "0")
     got = L.fa_sweep_plan(50_000, 50_048, L.FA_BF16)
     assert (got["Q"], got["W"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == \
         (8, 6256, 4, 2, 4, 256, 0)
+    got = L.fa_sweep_plan(50_000, 50_048, L.FA_F32)
+    assert (got["Q"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == (8, 7, 1, 4, 256, 0)
+    got = L.fa_sweep_plan(100_000, 80_000, L.FA_BF16)
+    assert (got["Q"], got["W"], got["S"], got["R"]) == (8, 10_000, 5, 1)
+
+
+def test_tensor_core_sweep_shape_behind_its_switch(monkeypatch):
+    # two 128-thread CTAs per SM, clusters of 16 and 7 rows per step at the
+    # 50k workload's width
+    monkeypatch.setenv("FA_SWEEP_KIND", "2")
+    got = L.fa_sweep_plan(50_000, 50_048, L.FA_BF16)
+    assert (got["Q"], got["W"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == \
+        (16, 3128, 4, 7, 2, 128, 2)
+    got = L.fa_sweep_plan(100_000, 80_000, L.FA_BF16)
+    assert (got["Q"], got["W"], got["S"], got["R"], got["NT"], got["kind"]) == \
+        (16, 5000, 3, 8, 256, 2)
 
 
 def _smem(p, b):
@@ -114,8 +116,10 @@ def _smem_mma(p):
     return (p["NS"] * p["R"] + 3) * rs + 16 + 8 * 8 + (p["NT"] // 32 * 8 + 4 * 16 * 8) * 4
 
 
+@pytest.mark.parametrize("kind", [0, 2])
 @pytest.mark.parametrize("dtype", [L.FA_BF16, L.FA_F32])
-def test_sweep_plan_invariants_at_every_width(dtype):
+def test_sweep_plan_invariants_at_every_width(dtype, kind, monkeypatch):
+    monkeypatch.setenv("FA_SWEEP_KIND", str(kind))
     V, b = (8, 2) if dtype == L.FA_BF16 else (4, 4)
     n_mma = 0
     for ld in range(128, MAX_ROW + 1, 128):
@@ -134,8 +138,10 @@ def test_sweep_plan_invariants_at_every_width(dtype):
         assert p["R"] in (1, 2, 4) and 2 <= p["NS"] <= 8
         per_sm = (4 if p["S"] * V <= 16 else 2) if p["NT"] == 256 else 1
         assert per_sm * (_smem(p, b) + SMEM_RESERVED_PER_CTA) <= SMEM_PER_SM, (ld, p)
-    if dtype == L.FA_BF16:
+    if dtype == L.FA_BF16 and kind == 2:
         assert n_mma > 0.8 * (MAX_ROW // 128)     # every width up to ~167k
+    else:
+        assert n_mma == 0
     with pytest.raises(L.FastAlignError) as ei:
         L.fa_sweep_plan(4096, MAX_ROW + 128, dtype)
     assert ei.value.status == L.FA_ERR_UNSUPPORTED
@@ -145,14 +151,14 @@ def test_sweep_plan_switches_and_errors(monkeypatch):
     monkeypatch.setenv("FA_SWEEP_Q", "2")
     assert L.fa_sweep_plan(10_000, 10_112, L.FA_BF16)["Q"] == 2
     monkeypatch.setenv("FA_SWEEP_Q", "")
+    monkeypatch.setenv("FA_SWEEP_KIND", "2")
     monkeypatch.setenv("FA_SWEEP_MB", "1")
     assert L.fa_sweep_plan(10_000, 10_112, L.FA_BF16)["NT"] == 256
     monkeypatch.delenv("FA_SWEEP_MB")
-    monkeypatch.setenv("FA_SWEEP_KIND", "0")
+    monkeypatch.delenv("FA_SWEEP_KIND")
     monkeypatch.setenv("FA_SWEEP_NT", "512")
     assert L.fa_sweep_plan(10_000, 10_112, L.FA_BF16)["NT"] == 512
     monkeypatch.delenv("FA_SWEEP_NT")
-    monkeypatch.delenv("FA_SWEEP_KIND")
     for args in [(0, 128, L.FA_BF16), (10, 100, L.FA_BF16), (10, 128, 7)]:
         with pytest.raises(L.FastAlignError) as ei:
             L.fa_sweep_plan(*args)

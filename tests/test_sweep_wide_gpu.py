@@ -82,9 +82,9 @@ def test_workload_sweep_shape_matches_oracle(case, monkeypatch, dtype, q):
 # last step for every R), 4700 columns (ld 4736: a partial last column pair
 # and padding columns in the last slab)
 M1, M2 = 1003, 4700
-MMA_SHAPES = ([{"FA_SWEEP_MB": mb, "FA_SWEEP_Q": q} for mb in (1, 2) for q in (1, 2, 4, 8, 16)]
-              + [{"FA_SWEEP_MB": 2, "FA_SWEEP_Q": 4, "FA_SWEEP_R": r} for r in (6, 7)]
-              + [{"FA_SWEEP_MB": 1, "FA_SWEEP_Q": 2, "FA_SWEEP_R": r} for r in (4, 5)])
+MMA_SHAPES = ([{"FA_SWEEP_KIND": 2, "FA_SWEEP_MB": mb, "FA_SWEEP_Q": q} for mb in (1, 2) for q in (1, 2, 4, 8, 16)]
+              + [{"FA_SWEEP_KIND": 2, "FA_SWEEP_MB": 2, "FA_SWEEP_Q": 4, "FA_SWEEP_R": r} for r in (6, 7)]
+              + [{"FA_SWEEP_KIND": 2, "FA_SWEEP_MB": 1, "FA_SWEEP_Q": 2, "FA_SWEEP_R": r} for r in (4, 5)])
 
 
 @pytest.fixture(scope="module")
