@@ -45,7 +45,7 @@ def test_oracle_never_imports_the_package():
 
 def test_bench_uses_the_oracle_only_in_its_cpu_legs():
     tree, imps = _imports(os.path.join(ROOT, "bench.py"))
-    allowed = {"_cpu_sample"}          # shared by the cpu_baseline leg and --impl reference
+    allowed = {"_oracle_run"}          # shared by the cpu_baseline leg and --impl reference
     funcs = [f for f in ast.walk(tree) if isinstance(f, ast.FunctionDef)]
     for m, node in imps:
         if m.split(".")[0] != "oracle":
