@@ -196,8 +196,14 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nsteps = (n1 + R - 1) / R;
   const int T = g < nsteps ? (nsteps - 1 - g) / G + 1 : 0;   // cluster-uniform
-  const TK* Kslab = K + (int64_t)q * W;
-  const uint32_t row_bytes = (uint32_t)W * sizeof(TK);
+  // column slab of CTA q: the row's ld / V 16-byte units split as evenly as
+  // possible (the first ld/V mod Q slabs one unit wider); W, the widest
+  // slab, is the ring's row pitch
+  const int units = (int)(ld / V), ubase = units / Q, urem = units - ubase * Q;
+  const int Wq = V * (ubase + (q < urem ? 1 : 0));
+  const int64_t off = (int64_t)V * (q * ubase + min(q, urem));
+  const TK* Kslab = K + off;
+  const uint32_t row_bytes = (uint32_t)Wq * sizeof(TK);
   const uint32_t xch_bytes = (uint32_t)(Q * R * 4);
 
   if (tid == 0) {
@@ -222,9 +228,9 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
     const int e0 = (s * NT + tid) * V;
 #pragma unroll
     for (int k = 0; k < V2; ++k) {
-      const int64_t col = (int64_t)q * W + e0 + 2 * k;
-      const float a = (e0 < W && col < n2) ? expf(log_v[col]) : 0.f;
-      const float b = (e0 < W && col + 1 < n2) ? expf(log_v[col + 1]) : 0.f;
+      const int64_t col = off + e0 + 2 * k;
+      const float a = (e0 < Wq && col < n2) ? expf(log_v[col]) : 0.f;
+      const float b = (e0 < Wq && col + 1 < n2) ? expf(log_v[col + 1]) : 0.f;
       vv[s][k] = pk2(a, b);
       acc[s][k] = pk2(0.f, 0.f);
     }
@@ -238,13 +244,13 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int e0 = (s * NT + tid) * V;
-    voff[s] = (uint32_t)((e0 < W ? e0 : W - V) * (int)sizeof(TK));
+    voff[s] = (uint32_t)((e0 < Wq ? e0 : Wq - V) * (int)sizeof(TK));
   }
   const uint32_t ring_s = smem_u32(ring);
   const uint32_t rowb = (uint32_t)W * sizeof(TK);
   // vectors s < S-1 are inside the slab for every thread; the last one only
   // for the first warps: skip it warp-uniformly where no lane has one
-  const bool last_ok = ((S - 1) * NT + warp * 32) * V < W;
+  const bool last_ok = ((S - 1) * NT + warp * 32) * V < Wq;
 
   // producer: step t goes to stage t % NS
   int issued = 0;   // meaningful in thread 0 only
@@ -356,7 +362,15 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
           case 2: sum_slots<R, 2>(xs, rsum); break;
           case 4: sum_slots<R, 4>(xs, rsum); break;
           case 8: sum_slots<R, 8>(xs, rsum); break;
-          default: sum_slots<R, 16>(xs, rsum); break;
+          case 16: sum_slots<R, 16>(xs, rsum); break;
+          default:   // other cluster sizes: the same CTA order, not unrolled
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              float a = 0.f;
+              for (int c = 0; c < Q; ++c) a += xs[c * R + r];
+              rsum[r] = a;
+            }
+            break;
         }
       } else {
 #pragma unroll
@@ -427,8 +441,8 @@ __global__ void __launch_bounds__(NT, sweep_ctas_per_sm(NT, S * KT<TK>::V)) k_sw
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int e0 = (s * NT + tid) * V;
-    if (e0 < W) {
-      float* dst = colpart + (int64_t)g * ld + (int64_t)q * W + e0;
+    if (e0 < Wq) {
+      float* dst = colpart + (int64_t)g * ld + off + e0;
 #pragma unroll
       for (int k = 0; k < V2; k += 2) {
         const float2 a = upk2(acc[s][k]), b = upk2(acc[s][k + 1]);
@@ -642,13 +656,21 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   int smax = NT == 1024 ? (bf16 ? 3 : 6) : (bf16 ? kSmaxBF16 : kSmaxF32);
   const int smax_env = env_int("FA_SWEEP_SMAX", 0);
   if (smax_env > 0 && smax_env < smax) smax = smax_env;
+  // BF16: any cluster size from 1 to 16.  The row's ld / V 16-byte units
+  // are split as evenly as possible over the Q CTAs (slab widths differ by
+  // at most one unit), so the smallest cluster that fits is not limited to
+  // the divisors of ld: at 50k, 5 CTAs with one row per step instead of 8
+  // CTAs with two (measured 0.64 -> see the design notes).  FP32, already
+  // at the copy peak with power-of-two clusters, keeps them
+  // (FA_SWEEP_ANYQ=1/0 forces either rule).  W is the widest slab.
+  const int64_t units = ld / V;
+  const bool anyq = env_int("FA_SWEEP_ANYQ", bf16 ? 1 : 0) != 0;
   for (int pass = 0; pass < 2 && sp.Q == 0; ++pass) {
     const int min_ns = pass == 0 ? 3 : 2;
-    for (int Q = 1; Q <= kMaxQ && sp.Q == 0; Q *= 2) {
+    for (int Q = 1; Q <= kMaxQ && sp.Q == 0; Q = anyq ? Q + 1 : 2 * Q) {
       if (Qforce && Q != Qforce) continue;
-      if (ld % Q) continue;
-      const int64_t W = ld / Q;
-      if ((W * (int64_t)b) % 16) continue;
+      if (units < Q) continue;
+      const int64_t W = V * ((units + Q - 1) / Q);
       const int S = (int)((W + (int64_t)NT * V - 1) / ((int64_t)NT * V));
       if (S > smax) continue;
       const size_t budget = kSmemBudget / sweep_ctas_per_sm(NT, S * V);

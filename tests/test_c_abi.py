@@ -28,7 +28,7 @@ def test_plain_c_program_uses_the_abi(tmp_path):
     assert r.returncode == 0, r.stderr
     lines = dict(l.split(" ", 1) for l in r.stdout.strip().splitlines())
     assert lines["params"] == "10 1 0.05 0.50"
-    assert lines["plan"] == "0 8 6256 4 2 4 256"
+    assert lines["plan"] == "0 5 10016 5 1 5 256"
     # rows 0..2 each see the other two, node 3 is isolated
     assert lines["csr"] == "0 6 0 2 4 6 6 1 0.50"
     assert lines["error"] == "1 1"

@@ -78,13 +78,23 @@ def test_csr_argument_errors():
 
 
 def test_sweep_shapes_of_the_measured_workloads():
+    # BF16: the smallest cluster of any size whose widest slab fits six
+    # 16-byte vectors per thread -- 5 CTAs at 50k (slabs of 1252 or 1251
+    # vectors), one row per step
     got = L.fa_sweep_plan(50_000, 50_048, L.FA_BF16)
     assert (got["Q"], got["W"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == \
-        (8, 6256, 4, 2, 4, 256, 0)
+        (5, 10016, 5, 1, 5, 256, 0)
     got = L.fa_sweep_plan(50_000, 50_048, L.FA_F32)
     assert (got["Q"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == (8, 7, 1, 4, 256, 0)
     got = L.fa_sweep_plan(100_000, 80_000, L.FA_BF16)
-    assert (got["Q"], got["W"], got["S"], got["R"]) == (8, 10_000, 5, 1)
+    assert (got["Q"], got["W"], got["S"], got["R"]) == (7, 11_432, 6, 1)
+
+
+def test_power_of_two_clusters_behind_their_switch(monkeypatch):
+    monkeypatch.setenv("FA_SWEEP_ANYQ", "0")
+    got = L.fa_sweep_plan(50_000, 50_048, L.FA_BF16)
+    assert (got["Q"], got["W"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == \
+        (8, 6256, 4, 2, 4, 256, 0)
 
 
 def test_tensor_core_sweep_shape_behind_its_switch(monkeypatch):
@@ -124,8 +134,14 @@ def test_sweep_plan_invariants_at_every_width(dtype, kind, monkeypatch):
     n_mma = 0
     for ld in range(128, MAX_ROW + 1, 128):
         p = L.fa_sweep_plan(4096, ld, dtype)
-        assert p["Q"] in (1, 2, 4, 8, 16) and p["kind"] in ((0, 2) if dtype == L.FA_BF16 else (0,))
-        assert p["Q"] * p["W"] == ld and (p["W"] * b) % 16 == 0
+        assert p["kind"] in ((0, 2) if dtype == L.FA_BF16 else (0,))
+        if p["kind"] == 0 and dtype == L.FA_BF16:
+            # any cluster size; slabs of ceil or floor of ld / V / Q vectors
+            assert 1 <= p["Q"] <= 16
+            assert p["W"] == V * -(-(ld // V) // p["Q"]) and (p["W"] * b) % 16 == 0
+        else:
+            assert p["Q"] in (1, 2, 4, 8, 16)
+            assert p["Q"] * p["W"] == ld and (p["W"] * b) % 16 == 0
         assert (p["S"] - 1) * p["NT"] * V < p["W"] <= p["S"] * p["NT"] * V
         assert 1 <= p["G"] <= (4096 + p["R"] - 1) // p["R"]
         if p["kind"] == 2:

@@ -38,6 +38,9 @@ SHAPES = (
     [("f32", {"FA_SWEEP_NT": nt, "FA_SWEEP_Q": q}) for nt in (256, 512) for q in (1, 2, 4, 8, 16)]
     + [("bf16", {"FA_SWEEP_KIND": 0, "FA_SWEEP_NT": nt, "FA_SWEEP_Q": q})
        for nt in (256, 512) for q in (1, 2, 4, 8, 16)]
+    # clusters of any size: uneven column slabs
+    + [("bf16", {"FA_SWEEP_KIND": 0, "FA_SWEEP_Q": q}) for q in (3, 5, 7, 9, 13)]
+    + [("f32", {"FA_SWEEP_ANYQ": 1, "FA_SWEEP_Q": q}) for q in (3, 6, 11)]
     # the tensor-core row pass (BF16): CTAs per SM x cluster size x rows per step
     + [("bf16", {"FA_SWEEP_KIND": 2, "FA_SWEEP_MB": mb, "FA_SWEEP_Q": q}) for mb in (1, 2) for q in (1, 2, 4, 8, 16)]
     + [("bf16", {"FA_SWEEP_KIND": 2, "FA_SWEEP_MB": 2, "FA_SWEEP_Q": 4, "FA_SWEEP_R": r}) for r in (6, 7)]

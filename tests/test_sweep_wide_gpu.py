@@ -60,11 +60,11 @@ def _run(K, lv0, dtype):
         al.close()
 
 
-@pytest.mark.parametrize("q", [0, 16])
+@pytest.mark.parametrize("q", [0, 8, 16])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_workload_sweep_shape_matches_oracle(case, monkeypatch, dtype, q):
-    """q = 0: the planner's own shape for this width (the bench's);
-    q = 16: the largest cluster."""
+    """q = 0: the planner's own shape for this width (the bench's); q = 8:
+    the power-of-two cluster; q = 16: the largest cluster."""
     from paper_2607_11952_gb300 import _lib as L
     K, lv0, u, v = case
     if q:
