@@ -225,19 +225,19 @@ fa_status fa_ctx_last_sweep_ms(const fa_ctx* ctx, double* ms, int32_t* n);
  * Learned warm start of the Sinkhorn solves.  The paper has no learned
  * component: this is a small 2-layer graph network on the column graph
  * G2 (hidden width 64, BF16 weights, FP32 accumulation) that predicts the
- * correction y = log v* - log v1 between the converged column scaling of a
- * solve and its cold first column update, so that fa_sinkhorn can start
- * from warm_log_v = log v1 + prediction.
+ * change of the correction y = log v* - log v1 between the converged
+ * column scaling of a solve and its cold first column update, so that
+ * fa_sinkhorn can start from warm_log_v = log v1 + c_prev + prediction.
  *
  *   AF = Abar F,  A1 = AF W1 + b1,  H = relu(A1),  z2 = H w2,
  *   a  = Abar z2 + c,
  *   L  = 1/n sum_j ((a_j - mean a) - (y_j - mean y))^2   (gauge invariant)
  *
- * Parameters (FP32 master copy, FA_GNN_NPARAMS floats): W1 [3 x 64,
+ * Parameters (FP32 master copy, FA_GNN_NPARAMS floats): W1 [6 x 64,
  * row-major] | b1 [64] | w2 [64] | c.  The forward pass reads BF16 copies
  * of W1 and w2 refreshed by fa_gnn_set_params and fa_gnn_adam_step.
  * ====================================================================== */
-#define FA_GNN_FIN 3
+#define FA_GNN_FIN 6
 #define FA_GNN_HIDDEN 64
 #define FA_GNN_NPARAMS (FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1)
 
@@ -255,14 +255,22 @@ fa_status fa_gnn_get_params(const fa_gnn* g, float* host_theta);
  * -1 if n < 1. */
 int64_t fa_gnn_workspace_floats(int32_t n);
 
-/* Per-node inputs F (device, n x 3 row-major) of the column graph g2:
- * (log_v1_j - mean log_v1, corr_prev_j - mean corr_prev, log(1 + deg_j))
- * (potentials are defined up to a constant, so both are centred); corr_prev
- * (device, n, nullable = zeros) is the previous solve's correction.
- * ws: workspace of fa_gnn_workspace_floats(n). */
+/* Per-node inputs F (device, n x FA_GNN_FIN row-major) of the column graph
+ * g2, column j:
+ *   0  log_v1_j - mean log_v1        (the solve's cold first column update)
+ *   1  corr_prev_j - mean corr_prev  (the previous solve's correction)
+ *   2  log(1 + deg_j)
+ *   3  pot_prev_j - mean pot_prev    (the previous solve's converged log v)
+ *   4  anchor_mask_j                 (1 if column j is an anchor's partner)
+ *   5  log(1 + outer_index)          (outer iterations done before this one)
+ * Potentials are defined up to a constant, so they are centred.  corr_prev,
+ * pot_prev and anchor_mask are device vectors of n floats, each nullable
+ * (= zeros, as for the first solve); outer_index >= 0 (FA_ERR_ARG
+ * otherwise).  ws: workspace of fa_gnn_workspace_floats(n). */
 fa_status fa_gnn_features(const fa_graph* g2, const float* log_v1,
-                          const float* corr_prev, float* F, float* ws,
-                          fa_stream_t stream);
+                          const float* corr_prev, const float* pot_prev,
+                          const float* anchor_mask, int32_t outer_index, float* F,
+                          float* ws, fa_stream_t stream);
 /* a_out (device, n) = model(F) on graph g; keeps activations in ws. */
 fa_status fa_gnn_forward(fa_gnn* m, const fa_graph* g, const float* F,
                          float* ws, float* a_out, fa_stream_t stream);

@@ -7,7 +7,7 @@ be checked.
 
 Model (a 2-layer graph network on the column graph G2, hidden width 64):
 
-    AF  = Abar F                       (n x 3, neighbourhood mean of features)
+    AF  = Abar F                       (n x 6, neighbourhood mean of features)
     A1  = AF W1 + b1                   (n x 64)
     H   = max(A1, 0)
     z2  = H w2                         (n)
@@ -28,12 +28,12 @@ import numpy as np
 import scipy.sparse as sp
 
 HIDDEN = 64
-FIN = 3
+FIN = 6
 N_PARAMS = FIN * HIDDEN + HIDDEN + HIDDEN + 1   # W1, b1, w2, c
 
 
 def unpack(theta: np.ndarray):
-    """Parameter vector layout: W1 (3 x 64, row-major), b1 (64), w2 (64), c."""
+    """Parameter vector layout: W1 (FIN x 64, row-major), b1 (64), w2 (64), c."""
     theta = np.asarray(theta, dtype=np.float64)
     o = 0
     W1 = theta[o:o + FIN * HIDDEN].reshape(FIN, HIDDEN)
@@ -88,10 +88,18 @@ def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def features(Abar_deg: np.ndarray, log_v1: np.ndarray, corr_prev: np.ndarray) -> np.ndarray:
-    """Per-node inputs: centred cold first column update, centred previous
-    correction (potentials are defined up to a constant), log(1 + degree)."""
+def features(Abar_deg: np.ndarray, log_v1: np.ndarray, corr_prev: np.ndarray,
+             pot_prev: np.ndarray | None = None, anchor_mask: np.ndarray | None = None,
+             outer_index: int = 0) -> np.ndarray:
+    """Per-node inputs of column node j: the centred cold first column
+    update, the centred previous correction and the centred previous
+    converged potential (potentials are defined up to a constant),
+    log(1 + degree), the anchor flag and log(1 + outer iterations done)."""
     lv = np.asarray(log_v1, np.float64)
+    n = lv.shape[0]
     cp = np.asarray(corr_prev, np.float64)
+    pp = np.zeros(n) if pot_prev is None else np.asarray(pot_prev, np.float64)
+    am = np.zeros(n) if anchor_mask is None else np.asarray(anchor_mask, np.float64)
     return np.stack([lv - lv.mean(), cp - cp.mean(),
-                     np.log1p(np.asarray(Abar_deg, np.float64))], axis=1)
+                     np.log1p(np.asarray(Abar_deg, np.float64)),
+                     pp - pp.mean(), am, np.full(n, np.log1p(outer_index))], axis=1)

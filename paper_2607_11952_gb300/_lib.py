@@ -82,7 +82,7 @@ SIGNATURES = {
     "fa_gnn_set_params": (_i32, [_p, _p]),
     "fa_gnn_get_params": (_i32, [_p, _p]),
     "fa_gnn_workspace_floats": (_i64, [_i32]),
-    "fa_gnn_features": (_i32, [_p, _p, _p, _p, _p, _p]),
+    "fa_gnn_features": (_i32, [_p, _p, _p, _p, _p, _i32, _p, _p, _p]),
     "fa_gnn_forward": (_i32, [_p, _p, _p, _p, _p, _p]),
     "fa_gnn_backward": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p]),
     "fa_gnn_adam_step": (_i32, [_p, _p, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -96,7 +96,7 @@ SIGNATURES = {
                                  _i64]),
     "fa_sweep_plan": (_i32, [_i32, _i64, _i32, _p]),
 }
-FA_GNN_FIN, FA_GNN_HIDDEN = 3, 64
+FA_GNN_FIN, FA_GNN_HIDDEN = 6, 64
 FA_GNN_NPARAMS = FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1
 
 _lib = None
@@ -318,8 +318,10 @@ def fa_gnn_workspace_floats(n: int) -> int:
     return lib().fa_gnn_workspace_floats(n)
 
 
-def fa_gnn_features(g2, log_v1, corr_prev, F, ws, stream=None) -> None:
-    _check(lib().fa_gnn_features(g2, ptr(log_v1), ptr(corr_prev), ptr(F), ptr(ws),
+def fa_gnn_features(g2, log_v1, corr_prev, pot_prev, anchor_mask, outer_index, F, ws,
+                    stream=None) -> None:
+    _check(lib().fa_gnn_features(g2, ptr(log_v1), ptr(corr_prev), ptr(pot_prev),
+                                 ptr(anchor_mask), int(outer_index), ptr(F), ptr(ws),
                                  stream_ptr(stream)), "fa_gnn_features")
 
 

@@ -138,14 +138,16 @@ class Aligner:
         self.C_node = torch.empty((self.n1, self.ld), dtype=torch.float32, device=self.device)
         self.log_u = torch.empty(self.n1, dtype=torch.float32, device=self.device)
         self.log_v = torch.empty(self.n2, dtype=torch.float32, device=self.device)
+        self.anchors = None             # the anchor pairs of the last node_cost
 
     # -- Phase 1
     def node_cost(self, X1, X2, anchors: np.ndarray, stream=None):
         X1 = torch.as_tensor(X1, dtype=torch.float32).to(self.device).contiguous()
         X2 = torch.as_tensor(X2, dtype=torch.float32).to(self.device).contiguous()
         d = X1.shape[1] if X1.ndim == 2 else 0
+        self.anchors = np.asarray(anchors).reshape(-1, 2)
         L.fa_node_cost(self.ctx, X1 if d else None, X2 if d else None, d,
-                       np.asarray(anchors), self.C_node, stream)
+                       self.anchors, self.C_node, stream)
 
     def plan_init(self, stream=None):
         L.fa_plan_init(self.ctx, self.K, self.log_u, self.log_v, stream)

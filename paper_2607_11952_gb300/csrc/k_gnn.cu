@@ -10,7 +10,7 @@
 // W1 and w2 are used in BF16 (FP32 master copies are updated by Adam); all
 // accumulation is FP32.  Reductions over nodes are deterministic (per-block
 // partials summed in a fixed order).  Parameter vector layout:
-// W1 [3 x 64 row-major] | b1 [64] | w2 [64] | c.
+// W1 [FA_GNN_FIN x 64 row-major] | b1 [64] | w2 [64] | c.
 #include <math.h>
 
 #include "fa_internal.cuh"
@@ -24,7 +24,7 @@ constexpr int kOffB1 = kFin * kHid;
 constexpr int kOffW2 = kOffB1 + kHid;
 constexpr int kOffC = kOffW2 + kHid;
 
-// workspace (floats): AF n*3 | A1 n*64 | z2 n | g n | gz2 n | partials nb*kNP | scal 8
+// workspace (floats): AF n*kFin | A1 n*64 | z2 n | g n | gz2 n | partials nb*kNP | scal 8
 struct GnnWs {
   float *AF, *A1, *z2, *g, *gz2, *part, *scal;
   int nb;
@@ -51,60 +51,75 @@ int64_t gnn_workspace_floats(int n) {
 }
 
 // ------------------------------------------------------------ reductions
-// one block: out[0] = mean of x (and, when y != null, out[1] = mean of y)
+// one block: out[0] = mean of x; when y (z) != null, out[1] (out[2]) = mean
+// of y (z)
 __global__ void __launch_bounds__(1024) k_means(int n, const float* __restrict__ x,
-                                                const float* __restrict__ y, float* out) {
-  __shared__ double sx[32], sy[32];
-  double ax = 0.0, ay = 0.0;
+                                                const float* __restrict__ y,
+                                                const float* __restrict__ z, float* out) {
+  __shared__ double sx[32], sy[32], sz[32];
+  double ax = 0.0, ay = 0.0, az = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     ax += x[i];
     if (y) ay += y[i];
+    if (z) az += z[i];
   }
   for (int o = 16; o > 0; o >>= 1) {
     ax += __shfl_xor_sync(0xffffffffu, ax, o);
     ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
   }
-  if ((threadIdx.x & 31) == 0) { sx[threadIdx.x >> 5] = ax; sy[threadIdx.x >> 5] = ay; }
+  if ((threadIdx.x & 31) == 0) {
+    sx[threadIdx.x >> 5] = ax;
+    sy[threadIdx.x >> 5] = ay;
+    sz[threadIdx.x >> 5] = az;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tx = 0.0, ty = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tx += sx[w]; ty += sy[w]; }
+    double tx = 0.0, ty = 0.0, tz = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tx += sx[w]; ty += sy[w]; tz += sz[w]; }
     out[0] = (float)(tx / n);
     if (y) out[1] = (float)(ty / n);
+    if (z) out[2] = (float)(tz / n);
   }
 }
 
 // ------------------------------------------------------------ features
-// F[j] = (log_v1_j - mean log_v1, corr_prev_j - mean corr_prev, log(1 + deg_j));
-// both potentials are centred: they are defined up to a constant
+// F[j] = (log_v1_j - mean log_v1, corr_prev_j - mean corr_prev,
+//         log(1 + deg_j), pot_prev_j - mean pot_prev, anchor_j, log(1 + t));
+// the potentials are centred (they are defined up to a constant)
 __global__ void k_gnn_features(int n, const int32_t* __restrict__ rp, const float* __restrict__ lv,
-                               const float* __restrict__ corr, const float* __restrict__ mean,
-                               float* __restrict__ F) {
+                               const float* __restrict__ corr, const float* __restrict__ pot,
+                               const float* __restrict__ anc, float lt,
+                               const float* __restrict__ mean, float* __restrict__ F) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  F[(size_t)j * kFin + 0] = lv[j] - mean[0];
-  F[(size_t)j * kFin + 1] = corr ? corr[j] - mean[1] : 0.f;
-  F[(size_t)j * kFin + 2] = log1pf((float)(rp[j + 1] - rp[j]));
+  float* f = F + (size_t)j * kFin;
+  f[0] = lv[j] - mean[0];
+  f[1] = corr ? corr[j] - mean[1] : 0.f;
+  f[2] = log1pf((float)(rp[j + 1] - rp[j]));
+  f[3] = pot ? pot[j] - mean[2] : 0.f;
+  f[4] = anc ? anc[j] : 0.f;
+  f[5] = lt;
 }
 
 // ------------------------------------------------------------ forward
 // AF[i] = sum_k Abar[i,k] F[k]  (thread per node)
-__global__ void k_gnn_agg3(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const float* __restrict__ val, const float* __restrict__ F,
-                           float* __restrict__ AF) {
+__global__ void k_gnn_agg(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const float* __restrict__ val, const float* __restrict__ F,
+                          float* __restrict__ AF) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  float a[kFin];
+#pragma unroll
+  for (int f = 0; f < kFin; ++f) a[f] = 0.f;
   for (int e = rp[i]; e < rp[i + 1]; ++e) {
     const float w = val[e];
-    const float* f = F + (size_t)ci[e] * kFin;
-    a0 += w * f[0];
-    a1 += w * f[1];
-    a2 += w * f[2];
+    const float* fk = F + (size_t)ci[e] * kFin;
+#pragma unroll
+    for (int f = 0; f < kFin; ++f) a[f] += w * fk[f];
   }
-  AF[(size_t)i * kFin + 0] = a0;
-  AF[(size_t)i * kFin + 1] = a1;
-  AF[(size_t)i * kFin + 2] = a2;
+#pragma unroll
+  for (int f = 0; f < kFin; ++f) AF[(size_t)i * kFin + f] = a[f];
 }
 
 // A1 = AF W1 + b1, z2 = relu(A1) w2  (warp per node, two hidden units per lane)
@@ -116,13 +131,16 @@ __global__ void __launch_bounds__(256) k_gnn_hidden(int n, const float* __restri
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
-  const float f0 = AF[(size_t)i * kFin], f1 = AF[(size_t)i * kFin + 1], f2 = AF[(size_t)i * kFin + 2];
+  float fi[kFin];
+#pragma unroll
+  for (int f = 0; f < kFin; ++f) fi[f] = AF[(size_t)i * kFin + f];
   float z = 0.f;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int h = lane + 32 * q;
-    const float a = f0 * __bfloat162float(W1[h]) + f1 * __bfloat162float(W1[kHid + h]) +
-                    f2 * __bfloat162float(W1[2 * kHid + h]) + theta[kOffB1 + h];
+    float a = theta[kOffB1 + h];
+#pragma unroll
+    for (int f = 0; f < kFin; ++f) a += fi[f] * __bfloat162float(W1[f * kHid + h]);
     A1[(size_t)i * kHid + h] = a;
     z += fmaxf(a, 0.f) * __bfloat162float(w2[h]);
   }
@@ -178,14 +196,18 @@ __global__ void __launch_bounds__(kGradThreads) k_gnn_grad_part(
     const __nv_bfloat16* __restrict__ w2, const float* __restrict__ gz2, float* __restrict__ part) {
   __shared__ float red[kGradThreads / 32][kNP - 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float dW[kFin][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, db[2] = {0.f, 0.f}, dw[2] = {0.f, 0.f};
+  float dW[kFin][2], db[2] = {0.f, 0.f}, dw[2] = {0.f, 0.f};
+#pragma unroll
+  for (int f = 0; f < kFin; ++f) dW[f][0] = dW[f][1] = 0.f;
   const float w2a = __bfloat162float(w2[lane]), w2b = __bfloat162float(w2[lane + 32]);
   const int base = (blockIdx.x * (kGradThreads / 32) + warp) * 4;
   for (int k = 0; k < 4; ++k) {
     const int i = base + k;
     if (i >= n) break;
     const float gi = gz2[i];
-    const float af[kFin] = {AF[(size_t)i * kFin], AF[(size_t)i * kFin + 1], AF[(size_t)i * kFin + 2]};
+    float af[kFin];
+#pragma unroll
+    for (int f = 0; f < kFin; ++f) af[f] = AF[(size_t)i * kFin + f];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float a = A1[(size_t)i * kHid + lane + 32 * q];
@@ -337,14 +359,17 @@ fa_status fa_gnn_get_params(const fa_gnn* g, float* host_theta) {
 int64_t fa_gnn_workspace_floats(int32_t n) { return n < 1 ? -1 : gnn_workspace_floats(n); }
 
 fa_status fa_gnn_features(const fa_graph* g2, const float* log_v1, const float* corr_prev,
+                          const float* pot_prev, const float* anchor_mask, int32_t outer_index,
                           float* F, float* ws, fa_stream_t stream) {
   if (!g2 || !log_v1 || !F || !ws) { set_error("fa_gnn_features: NULL argument"); return FA_ERR_ARG; }
+  if (outer_index < 0) { set_error("fa_gnn_features: outer_index < 0"); return FA_ERR_ARG; }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int n = g2->d.n;
   GnnWs w = ws_layout(ws, n);
-  k_means<<<1, 1024, 0, s>>>(n, log_v1, corr_prev, w.scal);
+  k_means<<<1, 1024, 0, s>>>(n, log_v1, corr_prev, pot_prev, w.scal);
   FA_LAUNCHED("k_means");
-  k_gnn_features<<<(n + 255) / 256, 256, 0, s>>>(n, g2->d.row_ptr, log_v1, corr_prev, w.scal, F);
+  k_gnn_features<<<(n + 255) / 256, 256, 0, s>>>(n, g2->d.row_ptr, log_v1, corr_prev, pot_prev,
+                                                 anchor_mask, log1pf((float)outer_index), w.scal, F);
   FA_LAUNCHED("k_gnn_features");
   return FA_OK;
 }
@@ -356,8 +381,8 @@ fa_status fa_gnn_forward(fa_gnn* g, const fa_graph* graph, const float* F, float
   const DevGraph& d = graph->d;
   const int n = d.n;
   GnnWs w = ws_layout(ws, n);
-  k_gnn_agg3<<<(n + 255) / 256, 256, 0, s>>>(n, d.row_ptr, d.col, d.val_row, F, w.AF);
-  FA_LAUNCHED("k_gnn_agg3");
+  k_gnn_agg<<<(n + 255) / 256, 256, 0, s>>>(n, d.row_ptr, d.col, d.val_row, F, w.AF);
+  FA_LAUNCHED("k_gnn_agg");
   k_gnn_hidden<<<(unsigned)(((int64_t)n * 32 + 255) / 256), 256, 0, s>>>(n, w.AF, g->W1, g->theta,
                                                                           g->w2, w.A1, w.z2);
   FA_LAUNCHED("k_gnn_hidden");
@@ -376,7 +401,7 @@ fa_status fa_gnn_backward(fa_gnn* g, const fa_graph* graph, const float* ws_in, 
   const DevGraph& d = graph->d;
   const int n = d.n;
   GnnWs w = ws_layout(const_cast<float*>(ws_in), n);
-  k_means<<<1, 1024, 0, s>>>(n, a_pred, target, w.scal);
+  k_means<<<1, 1024, 0, s>>>(n, a_pred, target, nullptr, w.scal);
   FA_LAUNCHED("k_means");
   k_gnn_resid<<<1, 1024, 0, s>>>(n, a_pred, target, w.scal, w.g, loss, grad);
   FA_LAUNCHED("k_gnn_resid");

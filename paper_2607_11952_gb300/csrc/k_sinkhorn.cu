@@ -478,7 +478,7 @@ static void* sweep_kernel(bool bf16, int S, int R, int NT) {
                   : R == 2 ? sweep_ptr<__nv_bfloat16, SS, 2>(NT) : sweep_ptr<__nv_bfloat16, SS, 1>(NT);
   FA_F(1) FA_F(2) FA_F(3) FA_F(4) FA_F(5) FA_F(6) FA_F(7) FA_F(8) FA_F(9)
   FA_F(10) FA_F(11) FA_F(12)
-  FA_B(1) FA_B(2) FA_B(3) FA_B(4) FA_B(5) FA_B(6)
+  FA_B(1) FA_B(2) FA_B(3) FA_B(4) FA_B(5) FA_B(6) FA_B(7)
 #undef FA_F
 #undef FA_B
   return nullptr;
@@ -655,7 +655,7 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   const int NT = (nt_env == 256 || nt_env == 1024) ? nt_env : 512;
   int smax = NT == 1024 ? (bf16 ? 3 : 6) : (bf16 ? kSmaxBF16 : kSmaxF32);
   const int smax_env = env_int("FA_SWEEP_SMAX", 0);
-  if (smax_env > 0 && smax_env < smax) smax = smax_env;
+  if (smax_env > 0 && (smax_env < smax || (bf16 && NT == 256 && smax_env == 7))) smax = smax_env;
   // BF16: any cluster size from 1 to 16.  The row's ld / V 16-byte units
   // are split as evenly as possible over the Q CTAs (slab widths differ by
   // at most one unit), so the smallest cluster that fits is not limited to

@@ -9,7 +9,9 @@ iterations have similar corrections, so the warm start is
 
 where c_prev is the previous solve's correction (0 at the first) and f, a
 2-layer graph network on the column graph G2 (hidden width 64, BF16
-weights), predicts the change of the correction, c - c_prev.  With f = 0
+weights), predicts the change of the correction, c - c_prev, from per-column
+inputs: the cold update log v1, c_prev, the previous converged potential
+log v*_prev, the degree, the anchor flag and the outer-iteration index.  With f = 0
 this is the "previous correction" warm start; the network learns what that
 misses.  The plain cold start (no warm start) stays available and is the
 reference the model is judged against.  The model's forward, backward and Adam kernels are the library's
@@ -65,9 +67,11 @@ class WarmStartModel:
             self._ws[n] = w
         return w
 
-    def features(self, graph: api.Graph, log_v1, corr_prev, F=None):
+    def features(self, graph: api.Graph, log_v1, corr_prev, pot_prev=None, anchor_mask=None,
+                 outer_index: int = 0, F=None):
         F = torch.empty((graph.n, FIN), dtype=torch.float32, device=self.device) if F is None else F
-        L.fa_gnn_features(graph.handle, log_v1, corr_prev, F, self.ws(graph.n))
+        L.fa_gnn_features(graph.handle, log_v1, corr_prev, pot_prev, anchor_mask, outer_index,
+                          F, self.ws(graph.n))
         return F
 
     def predict(self, graph: api.Graph, F, out=None):
@@ -118,7 +122,7 @@ class WarmStarter:
     MAX_CORR = 20.0     # bound on a predicted change of the correction (log units)
 
     def __init__(self, aligner: api.Aligner, mode: str = "learned",
-                 model: WarmStartModel | None = None):
+                 model: WarmStartModel | None = None, anchors=None):
         if mode == "learned" and model is None:
             raise ValueError("learned warm start needs a model")
         self.al, self.mode, self.model = aligner, mode, model
@@ -126,9 +130,23 @@ class WarmStarter:
         n2 = aligner.n2
         self.log_v1 = torch.empty(n2, dtype=torch.float32, device=dev)
         self.corr = torch.zeros(n2, dtype=torch.float32, device=dev)
+        self.pot = torch.zeros(n2, dtype=torch.float32, device=dev)    # previous log v*
         self.warm = torch.empty(n2, dtype=torch.float32, device=dev)
         self.base = torch.empty(n2, dtype=torch.float32, device=dev)
         self.F = torch.empty((n2, FIN), dtype=torch.float32, device=dev)
+        self.t = 0                      # solves done
+        self._anchors = anchors         # default: the aligner's, at the first solve
+        self.anchor_mask = None
+
+    def _mask(self):
+        """1 at every column that is an anchor's partner (built once)."""
+        if self.anchor_mask is None:
+            a = self._anchors if self._anchors is not None else getattr(self.al, "anchors", None)
+            m = torch.zeros(self.al.n2, dtype=torch.float32)
+            if a is not None and len(a):
+                m[torch.as_tensor(np.asarray(a)[:, 1], dtype=torch.long)] = 1.0
+            self.anchor_mask = m.to(self.al.device)
+        return self.anchor_mask
 
     def before_solve(self):
         L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, 0.0, None, self.log_v1)
@@ -137,7 +155,8 @@ class WarmStarter:
         if self.mode == "prev":
             L.fa_vec_axpby(self.al.n2, 1.0, self.log_v1, 1.0, self.corr, self.warm)
             return self.warm
-        self.model.features(self.al.g2, self.log_v1, self.corr, self.F)
+        self.model.features(self.al.g2, self.log_v1, self.corr,
+                            self.pot if self.t > 0 else None, self._mask(), self.t, self.F)
         pred = self.model.predict(self.al.g2, self.F)
         # base = log v1 + c_prev, then warm = base + clamp(pred)
         L.fa_vec_axpby(self.al.n2, 1.0, self.log_v1, 1.0, self.corr, self.base)
@@ -146,16 +165,21 @@ class WarmStarter:
 
     def after_solve(self):
         L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, -1.0, self.log_v1, self.corr)
+        L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, 0.0, None, self.pot)
+        self.t += 1
 
     def state(self) -> dict:
         """What the next solve depends on besides the plan: the previous
-        solve's correction (host copy, for checkpoints)."""
-        return {"mode": self.mode, "corr": self.corr.cpu()}
+        solve's correction and converged potential, and the number of
+        solves done (host copies, for checkpoints)."""
+        return {"mode": self.mode, "corr": self.corr.cpu(), "pot": self.pot.cpu(), "t": self.t}
 
     def load_state(self, st: dict) -> None:
         if st.get("mode") != self.mode or tuple(st["corr"].shape) != tuple(self.corr.shape):
             raise ValueError("warm-start state of another mode or size")
         self.corr.copy_(st["corr"])
+        self.pot.copy_(st["pot"])
+        self.t = int(st["t"])
 
     def solve(self, max_iter: int, tol: float, check_every: int = 5):
         """One warm-started solve; if it meets NaN/Inf (a bad prediction),
@@ -213,7 +237,8 @@ def generate_solves(n_pairs: int, outer: int, seed: int = 7, tol: float = 1e-5,
         for t in range(outer):
             al.align_iter()
             warm = ws.before_solve()
-            F = model.features(G2, ws.log_v1, ws.corr)
+            F = model.features(G2, ws.log_v1, ws.corr, ws.pot if ws.t > 0 else None,
+                               ws._mask(), ws.t)
             c_prev = ws.corr.clone()
             al.sinkhorn(max_sweeps, tol, 10, warm)
             ws.after_solve()

@@ -146,16 +146,25 @@ def test_trained_network_beats_previous_correction_start():
     assert tot["learned"] < tot["prev"] < tot["cold"]
 
 
-def test_features_match_oracle():
-    """Inputs of the model: the centred cold column update, the centred
-    previous correction and log(1 + degree), against the oracle's."""
+@pytest.mark.parametrize("first", [False, True])
+def test_features_match_oracle(first):
+    """Inputs of the model: the centred cold column update, previous
+    correction and previous potential, log(1 + degree), the anchor flag and
+    the outer-iteration index, against the oracle's; first = True is the
+    first solve (no previous state given)."""
     from paper_2607_11952_gb300 import gnn
     graph, e, F, y, theta = _case(n=900, seed=6)
     rng = np.random.default_rng(6)
     lv1 = (rng.standard_normal(graph.n) - 9.0).astype(np.float32)
     corr = (rng.standard_normal(graph.n) + 3.0).astype(np.float32)
+    pot = (rng.standard_normal(graph.n) - 4.0).astype(np.float32)
+    mask = (rng.random(graph.n) < 0.05).astype(np.float32)
     m = gnn.WarmStartModel(theta)
-    got = m.features(graph, torch.from_numpy(lv1).cuda(), torch.from_numpy(corr).cuda())
-    deg = np.bincount(e.ravel(), minlength=graph.n)
-    want = G.features(deg, lv1, corr)
+    dev = lambda x: torch.from_numpy(x).cuda()   # noqa: E731
+    if first:
+        got = m.features(graph, dev(lv1), None, None, None, 0)
+        want = G.features(np.bincount(e.ravel(), minlength=graph.n), lv1, np.zeros(graph.n))
+    else:
+        got = m.features(graph, dev(lv1), dev(corr), dev(pot), dev(mask), 7)
+        want = G.features(np.bincount(e.ravel(), minlength=graph.n), lv1, corr, pot, mask, 7)
     np.testing.assert_allclose(got.cpu().numpy(), want, rtol=1e-5, atol=1e-5)

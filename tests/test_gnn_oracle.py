@@ -41,7 +41,8 @@ def test_loss_is_gauge_invariant():
 def test_forward_hand_example():
     # path 0-1-2; W1 picks feature 0 into unit 0; w2 = e_0; c = 0.5
     A = R.row_normalized(3, np.array([[0, 1], [1, 2]]))
-    F = np.array([[1.0, 0, 0], [-2.0, 0, 0], [3.0, 0, 0]])
+    F = np.zeros((3, G.FIN))
+    F[:, 0] = [1.0, -2.0, 3.0]
     theta = np.zeros(G.N_PARAMS)
     theta[0] = 1.0                       # W1[0, 0]
     theta[G.FIN * G.HIDDEN + G.HIDDEN] = 1.0   # w2[0]
@@ -64,10 +65,15 @@ def test_adam_constant_gradient_closed_form():
 
 def test_features_hand_values():
     # degrees (0, 1, 3); log v1 (1, 2, 6) has mean 3; c_prev (0.5, 0.5, 2)
-    # has mean 1; the third input is log(1 + degree)
+    # has mean 1; previous potential (-1, 0, 4) has mean 1; node 1 is an
+    # anchor's partner; two outer iterations done
     F = G.features(np.array([0, 1, 3]), np.array([1.0, 2.0, 6.0]),
-                   np.array([0.5, 0.5, 2.0]))
-    want = np.array([[-2.0, -0.5, 0.0],
-                     [-1.0, -0.5, np.log(2.0)],
-                     [3.0, 1.0, np.log(4.0)]])
+                   np.array([0.5, 0.5, 2.0]), np.array([-1.0, 0.0, 4.0]),
+                   np.array([0.0, 1.0, 0.0]), 2)
+    want = np.array([[-2.0, -0.5, 0.0, -2.0, 0.0, np.log(3.0)],
+                     [-1.0, -0.5, np.log(2.0), -1.0, 1.0, np.log(3.0)],
+                     [3.0, 1.0, np.log(4.0), 3.0, 0.0, np.log(3.0)]])
     np.testing.assert_allclose(F, want, rtol=0, atol=1e-15)
+    # the first solve: no previous correction, potential or anchors given
+    F0 = G.features(np.array([2]), np.array([5.0]), np.array([0.0]))
+    np.testing.assert_array_equal(F0, [[0.0, 0.0, np.log(3.0), 0.0, 0.0, 0.0]])
