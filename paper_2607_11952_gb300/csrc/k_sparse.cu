@@ -196,9 +196,11 @@ fa_status launch_normalize_rows(int n, int d, const float* X, int64_t ldx,
 // s_k, output row by binary search in the tile's row pointers), broadcasts
 // them and keeps kGU row gathers of D[k, j0:j0+128] in flight (lane l:
 // columns 4l..4l+3, 256 B per gather in BF16, 512 B in FP32).  A finished row
-// goes to a shared-memory tile (atomics only for a row shared with another
-// warp); the tile is then stored transposed, 32 consecutive i per column j
-// (NV floats per element).  blockIdx.x runs over row tiles first, so all row
+// goes to a shared-memory tile; a row split between warps (at most the first
+// and the last row of a warp's range) leaves one partial per warp in that
+// warp's head or tail slot, added in warp order afterwards, so the sums
+// are formed in a fixed order without atomics.  The tile is then stored
+// transposed, 32 consecutive i per column j (NV floats per element).  blockIdx.x runs over row tiles first, so all row
 // tiles of one 128-column panel of D run back-to-back and the panel
 // (n1 x 128 elements) stays in L2.
 constexpr int kGU = 8;     // gathers in flight per warp
@@ -246,6 +248,8 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
   // the transposed read over a half warp
   constexpr int RS = TJ * NV + 4;
   __shared__ __align__(16) float tile[TI * RS];
+  __shared__ __align__(16) float split_s[8][2][TJ * NV];   // [warp][head/tail][columns]
+  __shared__ int split_row[8][2];                          // row of each slot, -1 if unused
   __shared__ __align__(16) EdgeRec edges[8][32];
   __shared__ int rps[TI + 1];
   const int i0 = blockIdx.x * TI;
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
   for (int t = threadIdx.x; t < TI * RS / 4; t += blockDim.x)
     reinterpret_cast<float4*>(tile)[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (threadIdx.x <= TI) rps[threadIdx.x] = rp[min(i0 + (int)threadIdx.x, n1)];
+  if (threadIdx.x < 16) split_row[threadIdx.x >> 1][threadIdx.x & 1] = -1;
   __syncthreads();
   {
     const int E0 = rps[0], len = rps[TI] - E0;
@@ -270,11 +275,15 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
     auto flush = [&]() {
       if (cur >= 0) {
         float* dst = tile + cur * RS + 4 * lane * NV;
-        if (rps[cur] < eb || rps[cur + 1] > ee) {   // row shared with another warp
+        const bool starts_before = rps[cur] < eb, ends_after = rps[cur + 1] > ee;
+        if (starts_before || ends_after) {   // row split with another warp: a slot
+          const int slot = starts_before ? 0 : 1;
+          float* sp = &split_s[warp][slot][4 * lane * NV];
 #pragma unroll
           for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) atomicAdd(dst + c * NV + v, acc[c][v]);
+            for (int v = 0; v < NV; ++v) sp[c * NV + v] = acc[c][v];
+          if (lane == 0) split_row[warp][slot] = cur;
         } else if constexpr (NV == 2) {
           reinterpret_cast<float4*>(dst)[0] = make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]);
           reinterpret_cast<float4*>(dst)[1] = make_float4(acc[2][0], acc[2][1], acc[3][0], acc[3][1]);
@@ -321,6 +330,26 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
       __syncwarp();
     }
     flush();
+  }
+  __syncthreads();
+  // split rows: the warps' partials in warp order (head before tail)
+  for (int k = threadIdx.x; k < TJ * NV; k += blockDim.x) {
+    int row = -1;
+    float z = 0.f;
+    for (int w = 0; w < 8; ++w) {
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const int r = split_row[w][sl];
+        if (r < 0) continue;
+        if (r != row) {
+          if (row >= 0) tile[row * RS + k] = z;
+          row = r;
+          z = 0.f;
+        }
+        z += split_s[w][sl][k];
+      }
+    }
+    if (row >= 0) tile[row * RS + k] = z;
   }
   __syncthreads();
   // transposed store: warp w writes columns c = w, w+8, ...; lane = row
@@ -440,12 +469,14 @@ fa_status launch_spmm_left_T(const DevGraph& g1, int n2, int64_t ldd,
                              float* Wt, cudaStream_t s) {
   const bool two = vb != nullptr;
   // measured at 50k on GB300: the row-per-warp form is faster for the two
-  // value sets of Pass A in BF16 (17 vs 22 ms), equal for propagation
+  // value sets of Pass A in BF16 (17 vs 22 ms) and takes them always; for
+  // one value set (propagation) the forms are equal and FA_PASSA_ROWS=1
+  // selects the row form
   static const int form = [] {
     const char* v = getenv("FA_PASSA_ROWS");
     return v ? atoi(v) : -1;
   }();
-  if (form == 1 || (form != 0 && two)) {
+  if (form == 1 || two) {
     dim3 g2d((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 63) / 64));
     if (d_bf16) {
       auto* Dp = static_cast<const __nv_bfloat16*>(D);
@@ -460,15 +491,12 @@ fa_status launch_spmm_left_T(const DevGraph& g1, int n2, int64_t ldd,
     return FA_OK;
   }
   dim3 grid((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 127) / 128));
-  if (d_bf16) {
-    auto* Dp = static_cast<const __nv_bfloat16*>(D);
-    if (two) k_spmm_left_T<__nv_bfloat16, 2><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
-    else     k_spmm_left_T<__nv_bfloat16, 1><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
-  } else {
-    auto* Dp = static_cast<const float*>(D);
-    if (two) k_spmm_left_T<float, 2><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
-    else     k_spmm_left_T<float, 1><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
-  }
+  if (d_bf16)
+    k_spmm_left_T<__nv_bfloat16, 1><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale,
+                                                         static_cast<const __nv_bfloat16*>(D), Wt);
+  else
+    k_spmm_left_T<float, 1><<<grid, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale,
+                                                 static_cast<const float*>(D), Wt);
   FA_LAUNCHED("k_spmm_left_T");
   return FA_OK;
 }
@@ -567,12 +595,16 @@ __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162flo
 // lane-parallel (column index, both weights times the scaling s_l, and the
 // output column found by binary search in the tile's row pointers), then
 // broadcasts them and keeps kGU gathers of W^T[l, i0:i0+64] (one float4 per
-// lane: rows 2 lane, 2 lane + 1, both value sets) in flight.  Sums of a
-// column are flushed into shared memory with atomics (a column can span two
-// warps); the epilogue then walks rows, lanes over columns, so the C_node,
-// K_prev and X rows are coalesced.  Shared tiles are XOR-swizzled by row so
-// both the flush (lanes over rows) and the epilogue (lanes over columns) are
-// free of bank conflicts up to 2 ways.
+// lane: rows 2 lane, 2 lane + 1, both value sets) in flight.  The sums are
+// formed without atomics, in a fixed order: a column whose edges lie
+// wholly in one warp's range is stored into the shared tile by that warp;
+// a column split between warps (at most the first and the last column of a
+// warp's range) leaves one partial per warp in that warp's head or tail
+// slot, and the epilogue adds a split column's partials in warp order.  The
+// epilogue walks rows, lanes over columns, so the C_node, K_prev and X rows
+// are coalesced.  Shared tiles are XOR-swizzled by row so both the stores
+// (lanes over rows) and the epilogue (lanes over columns) are free of bank
+// conflicts up to 2 ways.  Two runs give bit-identical results.
 constexpr int kRT = 64;    // rows per tile
 constexpr int kCT = 64;    // columns per tile
 
@@ -586,6 +618,8 @@ __global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
     const float* __restrict__ Wt, CostEpi ep) {
   __shared__ float ze_s[kRT * kCT];
   __shared__ float zn_s[kRT * kCT];
+  __shared__ __align__(16) float4 split_s[8][2][kRT / 2];   // [warp][head/tail][lane]: a0 b0 a1 b1
+  __shared__ int split_col[8][2];                            // column of each slot, -1 if unused
   __shared__ __align__(16) EdgeRec edges[8][32];
   __shared__ int rps[kCT + 1];
   const int j0 = blockIdx.x * kCT, i0 = blockIdx.y * kRT;
@@ -595,6 +629,7 @@ __global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
     zn_s[t] = 0.f;
   }
   if (threadIdx.x <= kCT) rps[threadIdx.x] = rp[min(j0 + (int)threadIdx.x, n2)];
+  if (threadIdx.x < 16) split_col[threadIdx.x >> 1][threadIdx.x & 1] = -1;
   __syncthreads();
 
   // ---- gathers: Z_e[i, j] and Z_n[i, j] for rows 2 lane, 2 lane + 1
@@ -608,10 +643,17 @@ __global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
     float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
     auto flush = [&]() {
       if (cur >= 0) {
-        atomicAdd(&ze_s[sw_idx(r0, cur)], a0);
-        atomicAdd(&zn_s[sw_idx(r0, cur)], b0);
-        atomicAdd(&ze_s[sw_idx(r1, cur)], a1);
-        atomicAdd(&zn_s[sw_idx(r1, cur)], b1);
+        const bool starts_before = rps[cur] < eb, ends_after = rps[cur + 1] > ee;
+        if (!starts_before && !ends_after) {   // the whole column is this warp's
+          ze_s[sw_idx(r0, cur)] = a0;
+          zn_s[sw_idx(r0, cur)] = b0;
+          ze_s[sw_idx(r1, cur)] = a1;
+          zn_s[sw_idx(r1, cur)] = b1;
+        } else {                               // split: head (first) or tail slot
+          const int slot = starts_before ? 0 : 1;
+          split_s[warp][slot][lane] = make_float4(a0, b0, a1, b1);
+          if (lane == 0) split_col[warp][slot] = cur;
+        }
       }
       a0 = b0 = a1 = b1 = 0.f;
     };
@@ -649,6 +691,38 @@ __global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
       __syncwarp();
     }
     flush();
+  }
+  __syncthreads();
+  // ---- split columns: the warps' partials in warp order (head before
+  // tail within a warp: a warp's head column precedes its tail column)
+  {
+    if (threadIdx.x < kRT) {
+      const int row = threadIdx.x, ln = row >> 1, hi = row & 1;
+      int col = -1;
+      float za = 0.f, zb = 0.f;
+      for (int w = 0; w < 8; ++w) {
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+          const int c = split_col[w][sl];
+          if (c < 0) continue;
+          if (c != col) {
+            if (col >= 0) {
+              ze_s[sw_idx(row, col)] = za;
+              zn_s[sw_idx(row, col)] = zb;
+            }
+            col = c;
+            za = zb = 0.f;
+          }
+          const float4 v = split_s[w][sl][ln];
+          za += hi ? v.z : v.x;
+          zb += hi ? v.w : v.y;
+        }
+      }
+      if (col >= 0) {
+        ze_s[sw_idx(row, col)] = za;
+        zn_s[sw_idx(row, col)] = zb;
+      }
+    }
   }
   __syncthreads();
 
