@@ -355,6 +355,47 @@ fa_status fa_sinkhorn_step_static(const void* K, int32_t dtype, int32_t n1,
                                   int32_t* status, fa_stream_t stream);
 
 /* ----------------------------------------------------------------------
+ * Column-sharded Sinkhorn iteration (Algorithm 1, Phase 3; Eq. 3) -- the
+ * data path of a sweep whose columns of K are split over devices, each
+ * owning a column range [j0, j1).  One iteration is three calls instead of
+ * the fused pass of fa_sinkhorn:
+ *
+ *   fa_sinkhorn_shard_rows     partial row sums sum_{j in block b} K_ij v_j
+ *                              for every column block b of the range
+ *   fa_sinkhorn_shard_combine  u_i = mu_i / sum_b (partials), all blocks of
+ *                              all ranges added in block order (with
+ *                              several devices the blocks are gathered
+ *                              first: n1 floats per block)
+ *   fa_sinkhorn_shard_cols     column sums sum_i K_ij u_i of the range and
+ *                              the next column scaling v_j = nu_j / (.)
+ *
+ * Column blocks are FA_SHARD_BLOCK columns wide and fixed by ld alone, and
+ * every sum runs in a fixed order, so any split into ranges whose bounds
+ * are multiples of FA_SHARD_BLOCK (or ld) gives bit-identical results.
+ * A range's columns of K are read twice per iteration.
+ *
+ * j0 must be a multiple of FA_SHARD_BLOCK, j1 a multiple of it or ld,
+ * 0 <= j0 < j1 <= ld (FA_ERR_ARG otherwise).  row_partials: device float,
+ * fa_shard_blocks(ld) x n1 (block-major); shard_rows writes the range's
+ * blocks, shard_combine reads all of them.  log_v: device n2 (the current
+ * column scaling); log_u: device n1.  shard_cols reads log_u, writes
+ * log_v_next[j] for j in [j0, min(j1, n2)) and, when err is not NULL, the
+ * L1 error sum_{j in range} |v_j (sum_i K_ij u_i) - nu_j| of the plan
+ * (log_u, log_v) into *err (device double).  FA_ERR_NUMERIC bits (an
+ * all-zero row) stay in the context's status and are reported by the next
+ * fa_sinkhorn.  Asynchronous on `stream`.
+ * -------------------------------------------------------------------- */
+#define FA_SHARD_BLOCK 2048
+int64_t fa_shard_blocks(int64_t ld);
+fa_status fa_sinkhorn_shard_rows(fa_ctx* ctx, const void* K, const float* log_v, int64_t j0,
+                                 int64_t j1, float* row_partials, fa_stream_t stream);
+fa_status fa_sinkhorn_shard_combine(fa_ctx* ctx, const float* row_partials, float* log_u,
+                                    fa_stream_t stream);
+fa_status fa_sinkhorn_shard_cols(fa_ctx* ctx, const void* K, const float* log_u,
+                                 const float* log_v, int64_t j0, int64_t j1,
+                                 float* log_v_next, double* err, fa_stream_t stream);
+
+/* ----------------------------------------------------------------------
  * fa_sweep_plan -- the launch shape fa_sinkhorn would use for the fused
  * sweep (Algorithm 1, Phase 3) on n1 rows of ld columns (ld a positive multiple
  * of 128) in storage type dtype, from host logic only (no device query;

@@ -95,7 +95,13 @@ SIGNATURES = {
     "fa_graph_csr_host": (_i32, [_i32, _i64, _p, _p, ctypes.POINTER(_i64), _p, _p, _p, _p,
                                  _i64]),
     "fa_sweep_plan": (_i32, [_i32, _i64, _i32, _p]),
+    "fa_shard_blocks": (_i64, [_i64]),
+    "fa_sinkhorn_shard_rows": (_i32, [_p, _p, _p, _i64, _i64, _p, _p]),
+    "fa_sinkhorn_shard_combine": (_i32, [_p, _p, _p, _p]),
+    "fa_sinkhorn_shard_cols": (_i32, [_p, _p, _p, _p, _i64, _i64, _p, _p, _p]),
 }
+
+FA_SHARD_BLOCK = 2048
 FA_GNN_FIN, FA_GNN_HIDDEN = 6, 64
 FA_GNN_NPARAMS = FA_GNN_FIN * FA_GNN_HIDDEN + 2 * FA_GNN_HIDDEN + 1
 
@@ -364,3 +370,25 @@ def fa_plan_change(ctx, K_a, log_u_a, log_v_a, K_b, log_u_b, log_v_b, stream=Non
                                 ptr(log_u_b), ptr(log_v_b), ctypes.byref(out),
                                 stream_ptr(stream)), "fa_plan_change")
     return out.value
+
+
+def fa_shard_blocks(ld: int) -> int:
+    return int(lib().fa_shard_blocks(int(ld)))
+
+
+def fa_sinkhorn_shard_rows(ctx, K, log_v, j0, j1, row_partials, stream=None) -> None:
+    _check(lib().fa_sinkhorn_shard_rows(ctx, ptr(K), ptr(log_v), int(j0), int(j1),
+                                        ptr(row_partials), stream_ptr(stream)),
+           "fa_sinkhorn_shard_rows")
+
+
+def fa_sinkhorn_shard_combine(ctx, row_partials, log_u, stream=None) -> None:
+    _check(lib().fa_sinkhorn_shard_combine(ctx, ptr(row_partials), ptr(log_u),
+                                           stream_ptr(stream)), "fa_sinkhorn_shard_combine")
+
+
+def fa_sinkhorn_shard_cols(ctx, K, log_u, log_v, j0, j1, log_v_next, err=None,
+                           stream=None) -> None:
+    _check(lib().fa_sinkhorn_shard_cols(ctx, ptr(K), ptr(log_u), ptr(log_v), int(j0), int(j1),
+                                        ptr(log_v_next), ptr(err), stream_ptr(stream)),
+           "fa_sinkhorn_shard_cols")

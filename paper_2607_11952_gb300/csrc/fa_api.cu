@@ -602,6 +602,52 @@ fa_status fa_rank(fa_ctx* c, const void* K, const float* log_v, int32_t n_query,
   return launch_rank(c->n2, c->ld, K, is_bf16(c), c->v_scale, n_query, rows, cols, rank_out, s);
 }
 
+// ------------------------------------------------------------ column-sharded sweep
+int64_t fa_shard_blocks(int64_t ld) { return ld < 1 ? -1 : (ld + kShardBlock - 1) / kShardBlock; }
+
+static fa_status check_range(const fa_ctx* c, int64_t j0, int64_t j1, const char* who) {
+  if (j0 < 0 || j1 > c->ld || j0 >= j1 || j0 % kShardBlock != 0 ||
+      (j1 != c->ld && j1 % kShardBlock != 0)) {
+    set_error("%s: column range [%lld, %lld) must satisfy 0 <= j0 < j1 <= ld = %lld with j0 "
+              "a multiple of %d and j1 a multiple of it or ld",
+              who, (long long)j0, (long long)j1, (long long)c->ld, kShardBlock);
+    return FA_ERR_ARG;
+  }
+  return FA_OK;
+}
+
+fa_status fa_sinkhorn_shard_rows(fa_ctx* c, const void* K, const float* log_v, int64_t j0,
+                                 int64_t j1, float* row_partials, fa_stream_t stream) {
+  if (!c || !K || !log_v || !row_partials) { set_error("fa_sinkhorn_shard_rows: NULL argument"); return FA_ERR_ARG; }
+  FA_TRY(check_range(c, j0, j1, "fa_sinkhorn_shard_rows"));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  FA_TRY(launch_exp_vec(c->n2, log_v, c->v_scale, s));
+  return launch_shard_rows(c->n1, c->n2, c->ld, j0, j1, K, is_bf16(c), c->v_scale, row_partials, s);
+}
+
+fa_status fa_sinkhorn_shard_combine(fa_ctx* c, const float* row_partials, float* log_u,
+                                    fa_stream_t stream) {
+  if (!c || !row_partials || !log_u) { set_error("fa_sinkhorn_shard_combine: NULL argument"); return FA_ERR_ARG; }
+  return launch_shard_combine(c->n1, (int)fa_shard_blocks(c->ld), row_partials,
+                              1.0f / (float)c->n1, c->u_scale, log_u, c->status,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+fa_status fa_sinkhorn_shard_cols(fa_ctx* c, const void* K, const float* log_u, const float* log_v,
+                                 int64_t j0, int64_t j1, float* log_v_next, double* err,
+                                 fa_stream_t stream) {
+  if (!c || !K || !log_u || !log_v || !log_v_next) { set_error("fa_sinkhorn_shard_cols: NULL argument"); return FA_ERR_ARG; }
+  FA_TRY(check_range(c, j0, j1, "fa_sinkhorn_shard_cols"));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  FA_TRY(launch_exp_vec(c->n1, log_u, c->u_scale, s));
+  FA_TRY(launch_shard_cols(c->n1, c->ld, j0, j1, K, is_bf16(c), c->u_scale, c->colpart, s));
+  const int64_t jend = std::min<int64_t>(j1, c->n2);
+  if (jend <= j0) return FA_OK;          // a range of padding columns only
+  return launch_col_finalize((int)(jend - j0), c->ld, shard_col_groups(c->n1), c->colpart + j0,
+                             log_v + j0, 1.0f / (float)c->n2, log_v_next + j0, c->err_part,
+                             c->ticket, err ? err : c->err, c->status, s);
+}
+
 // ------------------------------------------------------------ sweep plan
 fa_status fa_sweep_plan(int32_t n1, int64_t ld, int32_t dtype, int32_t* out) {
   if (!out) { set_error("fa_sweep_plan: out is NULL"); return FA_ERR_ARG; }

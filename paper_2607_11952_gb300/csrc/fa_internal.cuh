@@ -155,6 +155,16 @@ fa_status launch_col_finalize(int n2, int64_t ld, int G, const float* colpart,
                               unsigned* ticket, double* err_out, int* status,
                               cudaStream_t s);
 
+// Column-sharded sweep (k_shard.cu)
+constexpr int kShardBlock = FA_SHARD_BLOCK;
+fa_status launch_shard_rows(int n1, int n2, int64_t ld, int64_t j0, int64_t j1, const void* K,
+                            bool bf16, const float* v, float* rowpart, cudaStream_t s);
+fa_status launch_shard_combine(int n1, int nblocks, const float* rowpart, float mu, float* u,
+                               float* log_u, int* status, cudaStream_t s);
+int shard_col_groups(int n1);
+fa_status launch_shard_cols(int n1, int64_t ld, int64_t j0, int64_t j1, const void* K, bool bf16,
+                            const float* u, float* colpart, cudaStream_t s);
+
 // Read-out
 fa_status launch_topk(int n1, int n2, int64_t ld, const void* K, bool bf16,
                       const float* log_v, int k, int32_t* idx, float* score,
