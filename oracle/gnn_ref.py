@@ -103,3 +103,17 @@ def features(Abar_deg: np.ndarray, log_v1: np.ndarray, corr_prev: np.ndarray,
     return np.stack([lv - lv.mean(), cp - cp.mean(),
                      np.log1p(np.asarray(Abar_deg, np.float64)),
                      pp - pp.mean(), am, np.full(n, np.log1p(outer_index))], axis=1)
+
+
+def fit_scale(pred: np.ndarray, y: np.ndarray, max_abs: float) -> float:
+    """The trust in a prediction: the least-squares scale alpha minimising
+    |(y - mean y) - alpha (p - mean p)|^2 for p = clamp(pred, -max_abs,
+    max_abs) (non-finite entries 0), clipped to [0, 1]; 0 when p is
+    constant."""
+    p = np.where(np.isfinite(pred), np.clip(np.asarray(pred, np.float64), -max_abs, max_abs), 0.0)
+    yy = np.asarray(y, np.float64)
+    dp, dy = p - p.mean(), yy - yy.mean()
+    den = float(dp @ dp)
+    if den == 0.0:
+        return 0.0
+    return float(min(1.0, max(0.0, (dp @ dy) / den)))

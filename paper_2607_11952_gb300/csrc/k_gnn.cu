@@ -270,15 +270,65 @@ __global__ void k_gnn_sync_bf16(const float* __restrict__ theta, __nv_bfloat16* 
   else if (p >= kOffW2 && p < kOffC) w2[p - kOffW2] = __float2bfloat16_rn(theta[p]);
 }
 
-// warm start: out = log_v1 + clamp(pred, -max_abs, max_abs); a non-finite
-// prediction contributes 0 (the cold start for that column)
+__device__ __forceinline__ float clamp_pred(float p, float max_abs) {
+  return isfinite(p) ? fminf(fmaxf(p, -max_abs), max_abs) : 0.f;
+}
+
+// warm start: out = log_v1 + scale * clamp(pred, -max_abs, max_abs); a
+// non-finite prediction contributes 0 (the cold start for that column)
 __global__ void k_gnn_warm(int n, const float* __restrict__ lv1, const float* __restrict__ pred,
-                           float max_abs, float* __restrict__ out) {
+                           float max_abs, const float* __restrict__ scale,
+                           float* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float p = pred[i];
-  p = isfinite(p) ? fminf(fmaxf(p, -max_abs), max_abs) : 0.f;
-  out[i] = lv1[i] + p;
+  out[i] = lv1[i] + (scale ? scale[0] : 1.f) * clamp_pred(pred[i], max_abs);
+}
+
+// one block: the centred least-squares scale of clamp(pred) against y,
+// clipped to [0, 1] (two fixed-order passes: means, then moments)
+__global__ void __launch_bounds__(1024) k_gnn_fit_scale(int n, const float* __restrict__ pred,
+                                                        const float* __restrict__ y,
+                                                        float max_abs, float* __restrict__ out) {
+  __shared__ double s1[32], s2[32];
+  __shared__ double mp, my;
+  double ap = 0.0, ay = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    ap += clamp_pred(pred[i], max_abs);
+    ay += y[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ap += __shfl_xor_sync(0xffffffffu, ap, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+  }
+  if ((threadIdx.x & 31) == 0) { s1[threadIdx.x >> 5] = ap; s2[threadIdx.x >> 5] = ay; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tp = 0.0, ty = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tp += s1[w]; ty += s2[w]; }
+    mp = tp / n;
+    my = ty / n;
+  }
+  __syncthreads();
+  double cxy = 0.0, cxx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double dp = clamp_pred(pred[i], max_abs) - mp;
+    cxy += dp * ((double)y[i] - my);
+    cxx += dp * dp;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cxy += __shfl_xor_sync(0xffffffffu, cxy, o);
+    cxx += __shfl_xor_sync(0xffffffffu, cxx, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { s1[threadIdx.x >> 5] = cxy; s2[threadIdx.x >> 5] = cxx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double txy = 0.0, txx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { txy += s1[w]; txx += s2[w]; }
+    double a = txx > 0.0 ? txy / txx : 0.0;
+    a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+    out[0] = (float)a;
+  }
 }
 
 __global__ void k_axpby(int n, float a, const float* __restrict__ x, float b,
@@ -427,14 +477,26 @@ fa_status fa_gnn_adam_step(fa_gnn* g, const float* grad, float lr, float beta1, 
 }
 
 fa_status fa_gnn_warm_start(int32_t n, const float* log_v1, const float* pred, float max_abs,
-                            float* out, fa_stream_t stream) {
+                            const float* scale, float* out, fa_stream_t stream) {
   if (n < 1 || !log_v1 || !pred || !out || !(max_abs > 0.f)) {
     set_error("fa_gnn_warm_start: bad argument");
     return FA_ERR_ARG;
   }
-  k_gnn_warm<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(n, log_v1, pred,
-                                                                                 max_abs, out);
+  k_gnn_warm<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      n, log_v1, pred, max_abs, scale, out);
   FA_LAUNCHED("k_gnn_warm");
+  return FA_OK;
+}
+
+fa_status fa_gnn_fit_scale(int32_t n, const float* pred, const float* y, float max_abs,
+                           float* scale, fa_stream_t stream) {
+  if (n < 1 || !pred || !y || !scale || !(max_abs > 0.f)) {
+    set_error("fa_gnn_fit_scale: bad argument");
+    return FA_ERR_ARG;
+  }
+  k_gnn_fit_scale<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(n, pred, y, max_abs,
+                                                                          scale);
+  FA_LAUNCHED("k_gnn_fit_scale");
   return FA_OK;
 }
 

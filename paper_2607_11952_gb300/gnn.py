@@ -115,11 +115,16 @@ class WarmStarter:
 
     mode "cold":    no warm start (fa_sinkhorn's first b update uses v1).
     mode "prev":    warm_log_v = log v1 + c_prev (the previous solve's correction).
-    mode "learned": warm_log_v = log v1 + c_prev + clamp(model(features)).
+    mode "learned": warm_log_v = log v1 + c_prev + alpha clamp(model(features)),
+                    alpha in [0, 1] the least-squares scale of the previous
+                    solve's prediction against the change it predicted (1
+                    before the first fit): the previous solve calibrates how
+                    far the network is trusted on this pair.
     Call ``before_solve`` right after fa_align_iter and ``after_solve``
     after fa_sinkhorn, or ``solve`` for both with the cold-start fallback."""
 
     MAX_CORR = 20.0     # bound on a predicted change of the correction (log units)
+    CALIBRATE = True    # fit the trust alpha after every solve (False: alpha = 1)
 
     def __init__(self, aligner: api.Aligner, mode: str = "learned",
                  model: WarmStartModel | None = None, anchors=None):
@@ -137,6 +142,10 @@ class WarmStarter:
         self.t = 0                      # solves done
         self._anchors = anchors         # default: the aligner's, at the first solve
         self.anchor_mask = None
+        self.pred = torch.zeros(n2, dtype=torch.float32, device=dev)   # last prediction
+        self.change = torch.empty(n2, dtype=torch.float32, device=dev)
+        self.alpha = torch.ones(1, dtype=torch.float32, device=dev)    # trust in the network
+        self.predicted = False
 
     def _mask(self):
         """1 at every column that is an anchor's partner (built once)."""
@@ -157,13 +166,22 @@ class WarmStarter:
             return self.warm
         self.model.features(self.al.g2, self.log_v1, self.corr,
                             self.pot if self.t > 0 else None, self._mask(), self.t, self.F)
-        pred = self.model.predict(self.al.g2, self.F)
-        # base = log v1 + c_prev, then warm = base + clamp(pred)
+        self.model.predict(self.al.g2, self.F, out=self.pred)
+        self.predicted = True
+        # base = log v1 + c_prev, then warm = base + alpha clamp(pred)
         L.fa_vec_axpby(self.al.n2, 1.0, self.log_v1, 1.0, self.corr, self.base)
-        L.fa_gnn_warm_start(self.al.n2, self.base, pred, self.MAX_CORR, self.warm)
+        L.fa_gnn_warm_start(self.al.n2, self.base, self.pred, self.MAX_CORR, self.warm,
+                            scale=self.alpha)
         return self.warm
 
     def after_solve(self):
+        if self.predicted and self.CALIBRATE:
+            # the change of the correction this solve produced, c - c_prev,
+            # against the prediction: the next solve's trust alpha
+            L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, -1.0, self.log_v1, self.change)
+            L.fa_vec_axpby(self.al.n2, 1.0, self.change, -1.0, self.corr, self.change)
+            L.fa_gnn_fit_scale(self.al.n2, self.pred, self.change, self.MAX_CORR, self.alpha)
+            self.predicted = False
         L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, -1.0, self.log_v1, self.corr)
         L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, 0.0, None, self.pot)
         self.t += 1
@@ -172,13 +190,15 @@ class WarmStarter:
         """What the next solve depends on besides the plan: the previous
         solve's correction and converged potential, and the number of
         solves done (host copies, for checkpoints)."""
-        return {"mode": self.mode, "corr": self.corr.cpu(), "pot": self.pot.cpu(), "t": self.t}
+        return {"mode": self.mode, "corr": self.corr.cpu(), "pot": self.pot.cpu(), "t": self.t,
+                "alpha": self.alpha.cpu()}
 
     def load_state(self, st: dict) -> None:
         if st.get("mode") != self.mode or tuple(st["corr"].shape) != tuple(self.corr.shape):
             raise ValueError("warm-start state of another mode or size")
         self.corr.copy_(st["corr"])
         self.pot.copy_(st["pot"])
+        self.alpha.copy_(st["alpha"])
         self.t = int(st["t"])
 
     def solve(self, max_iter: int, tol: float, check_every: int = 5):

@@ -6,9 +6,14 @@ which the oracle's CPU tests pin to the log form over whole runs).
 
 Tolerances (the FP32 path's, written here):
 * plan: ||T - T_ref||_F / ||T_ref||_F <= 1e-4;
-* column marginals: |m - m_ref|_inf <= 1e-6 / n2 + 1e-6 max m_ref (1e-6
-  relative to 1/n); row marginals within 1e-6 / n1 of mu (rows are exact
-  after the b update up to FP32 rounding of the row sums);
+* column marginals: |m - m_ref|_inf <= 1e-5 max m_ref.  After 20 outer
+  iterations the exponent x = -C_eff/eps of each Gibbs kernel entry is
+  formed in FP32 with |x| up to ~100, an absolute rounding error of up to
+  ~100 x 2^-24 x (a few operations) ~ 1e-5, i.e. a relative error of that
+  size in K and hence in a column sum; 1e-6 relative to 1/n (the bound
+  used for the shallow 1k run) is below what FP32 can promise here.  Row
+  marginals within 1e-6 / n1 of mu (rows are exact after the b update up to
+  FP32 rounding of the row sums);
 * top-10: every position whose value is separated from both neighbours in
   the sorted row by more than 1e-5 T_(1) holds the oracle's column;
 * Hits@1 within one test pair of the oracle's."""
@@ -63,7 +68,7 @@ def test_plan_and_marginals_10k(runs):
     print(f"plan {rel:.3e}; column marginals {dm * g.n2:.3e} x 1/n2; rows {dr * g.n1:.3e} x 1/n1")
     assert all(st == 0 and it == SINK for it, _, st in out["hist"])
     assert rel <= 1e-4
-    assert dm <= 1e-6 / g.n2 + 1e-6 * np.abs(mr).max()
+    assert dm <= 1e-5 * np.abs(mr).max()
     assert dr <= 1e-6 / g.n1
 
 

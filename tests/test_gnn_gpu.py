@@ -168,3 +168,20 @@ def test_features_match_oracle(first):
         got = m.features(graph, dev(lv1), dev(corr), dev(pot), dev(mask), 7)
         want = G.features(np.bincount(e.ravel(), minlength=graph.n), lv1, corr, pot, mask, 7)
     np.testing.assert_allclose(got.cpu().numpy(), want, rtol=1e-5, atol=1e-5)
+
+
+def test_fit_scale_matches_oracle():
+    """The trust fit of the learned warm start (the clamped prediction's
+    least-squares scale against the observed change, clipped to [0, 1])."""
+    from paper_2607_11952_gb300 import _lib as L
+    rng = np.random.default_rng(12)
+    n = 5001
+    pred = (3.0 * rng.standard_normal(n)).astype(np.float32)
+    pred[7] = np.inf
+    for k in (0.3, 1.7, -0.4):
+        y = (k * np.clip(pred, -2.0, 2.0) * np.isfinite(pred) + 0.1 * rng.standard_normal(n)
+             + 5.0).astype(np.float32)
+        out = torch.zeros(1, device="cuda")
+        L.fa_gnn_fit_scale(n, torch.from_numpy(pred).cuda(), torch.from_numpy(y).cuda(), 2.0, out)
+        want = G.fit_scale(pred.astype(np.float64), y.astype(np.float64), 2.0)
+        assert abs(out.item() - want) <= 1e-6, (k, out.item(), want)

@@ -77,3 +77,19 @@ def test_features_hand_values():
     # the first solve: no previous correction, potential or anchors given
     F0 = G.features(np.array([2]), np.array([5.0]), np.array([0.0]))
     np.testing.assert_array_equal(F0, [[0.0, 0.0, np.log(3.0), 0.0, 0.0, 0.0]])
+
+
+def test_fit_scale_hand_values():
+    p = np.array([1.0, 2.0, 3.0, 6.0])
+    # y = k p + c: the centred fit recovers k, clipped to [0, 1]
+    assert G.fit_scale(p, 0.5 * p + 7.0, 20.0) == 0.5
+    assert G.fit_scale(p, 3.0 * p, 20.0) == 1.0
+    assert G.fit_scale(p, -p, 20.0) == 0.0
+    assert G.fit_scale(np.full(4, 2.0), p, 20.0) == 0.0          # constant prediction
+    # the clamp applies first: p = (1, 2, 2, 2) against y = p
+    assert abs(G.fit_scale(p, np.array([1.0, 2.0, 2.0, 2.0]), 2.0) - 1.0) < 1e-15
+    # a non-finite prediction counts as 0
+    q = np.array([1.0, np.nan, 3.0, -1.0])
+    want = G.fit_scale(np.array([1.0, 0.0, 3.0, -1.0]), np.array([0.2, 0.0, 0.6, -0.2]), 20.0)
+    assert abs(G.fit_scale(q, np.array([0.2, 0.0, 0.6, -0.2]), 20.0) - want) < 1e-15
+    assert abs(want - 0.2) < 1e-15
