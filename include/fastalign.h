@@ -297,14 +297,16 @@ fa_status fa_gnn_warm_start(int32_t n, const float* log_v1, const float* pred,
 /* The least-squares scale of a prediction against the change it was meant
  * to predict, clipped to [0, 1]:
  *   p = clamp(pred, -max_abs, max_abs) (non-finite -> 0),
- *   *scale = clip( sum_j (p_j - mean p)(y_j - mean y) / sum_j (p_j - mean p)^2, 0, 1 )
- * (0 when p is constant).  Centred because potentials are defined up to a
+ *   a = clip( sum_j (p_j - mean p)(y_j - mean y) / sum_j (p_j - mean p)^2, 0, 1 )
+ * (0 when p is constant); with shrink != 0 the result is a rho^2, rho the
+ * correlation of p and y, so a prediction that explains little of y is
+ * trusted little.  Centred because potentials are defined up to a
  * constant.  pred, y: device vectors of n floats; scale: device scalar.
  * Fixed-order FP64 sums.  Used after each solve to damp the next solve's
  * prediction by how well the last one matched (0: the previous-correction
  * start, 1: the network's own prediction). */
 fa_status fa_gnn_fit_scale(int32_t n, const float* pred, const float* y, float max_abs,
-                           float* scale, fa_stream_t stream);
+                           int32_t shrink, float* scale, fa_stream_t stream);
 /* out = a x + b y on device vectors of n floats (y nullable = 0). */
 fa_status fa_vec_axpby(int32_t n, float a, const float* x, float b,
                        const float* y, float* out, fa_stream_t stream);

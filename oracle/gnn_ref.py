@@ -105,15 +105,19 @@ def features(Abar_deg: np.ndarray, log_v1: np.ndarray, corr_prev: np.ndarray,
                      pp - pp.mean(), am, np.full(n, np.log1p(outer_index))], axis=1)
 
 
-def fit_scale(pred: np.ndarray, y: np.ndarray, max_abs: float) -> float:
+def fit_scale(pred: np.ndarray, y: np.ndarray, max_abs: float, shrink: bool = False) -> float:
     """The trust in a prediction: the least-squares scale alpha minimising
     |(y - mean y) - alpha (p - mean p)|^2 for p = clamp(pred, -max_abs,
     max_abs) (non-finite entries 0), clipped to [0, 1]; 0 when p is
-    constant."""
+    constant.  shrink: alpha times the squared correlation of p and y."""
     p = np.where(np.isfinite(pred), np.clip(np.asarray(pred, np.float64), -max_abs, max_abs), 0.0)
     yy = np.asarray(y, np.float64)
     dp, dy = p - p.mean(), yy - yy.mean()
     den = float(dp @ dp)
     if den == 0.0:
         return 0.0
-    return float(min(1.0, max(0.0, (dp @ dy) / den)))
+    a = float(min(1.0, max(0.0, (dp @ dy) / den)))
+    if shrink:
+        vy = float(dy @ dy)
+        a *= float((dp @ dy) ** 2 / (den * vy)) if vy > 0.0 else 0.0
+    return a

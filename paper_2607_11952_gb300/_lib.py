@@ -89,7 +89,7 @@ SIGNATURES = {
                                 ctypes.c_float, _p]),
     "fa_vec_axpby": (_i32, [_i32, ctypes.c_float, _p, ctypes.c_float, _p, _p, _p]),
     "fa_gnn_warm_start": (_i32, [_i32, _p, _p, ctypes.c_float, _p, _p, _p]),
-    "fa_gnn_fit_scale": (_i32, [_i32, _p, _p, ctypes.c_float, _p, _p]),
+    "fa_gnn_fit_scale": (_i32, [_i32, _p, _p, ctypes.c_float, _i32, _p, _p]),
     "fa_sinkhorn_step_static": (_i32, [_p, _i32, _i32, _i32, _i64, _p, _p, _p, _p, _p, _p]),
     "fa_plan_change": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _p]),
     "fa_ctx_selftest_wait": (_i32, [_p, _p]),
@@ -357,9 +357,9 @@ def fa_gnn_warm_start(n, log_v1, pred, max_abs, out, scale=None, stream=None) ->
                                    ptr(out), stream_ptr(stream)), "fa_gnn_warm_start")
 
 
-def fa_gnn_fit_scale(n, pred, y, max_abs, scale, stream=None) -> None:
-    _check(lib().fa_gnn_fit_scale(int(n), ptr(pred), ptr(y), float(max_abs), ptr(scale),
-                                  stream_ptr(stream)), "fa_gnn_fit_scale")
+def fa_gnn_fit_scale(n, pred, y, max_abs, scale, shrink=False, stream=None) -> None:
+    _check(lib().fa_gnn_fit_scale(int(n), ptr(pred), ptr(y), float(max_abs), 1 if shrink else 0,
+                                  ptr(scale), stream_ptr(stream)), "fa_gnn_fit_scale")
 
 
 def fa_sinkhorn_step_static(K, dtype, n1, n2, ld, log_v, log_u, log_v_next, err, status=None,

@@ -288,8 +288,9 @@ __global__ void k_gnn_warm(int n, const float* __restrict__ lv1, const float* __
 // clipped to [0, 1] (two fixed-order passes: means, then moments)
 __global__ void __launch_bounds__(1024) k_gnn_fit_scale(int n, const float* __restrict__ pred,
                                                         const float* __restrict__ y,
-                                                        float max_abs, float* __restrict__ out) {
-  __shared__ double s1[32], s2[32];
+                                                        float max_abs, int shrink,
+                                                        float* __restrict__ out) {
+  __shared__ double s1[32], s2[32], s3[32];
   __shared__ double mp, my;
   double ap = 0.0, ay = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -309,24 +310,32 @@ __global__ void __launch_bounds__(1024) k_gnn_fit_scale(int n, const float* __re
     my = ty / n;
   }
   __syncthreads();
-  double cxy = 0.0, cxx = 0.0;
+  double cxy = 0.0, cxx = 0.0, cyy = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double dp = clamp_pred(pred[i], max_abs) - mp;
-    cxy += dp * ((double)y[i] - my);
+    const double dy = (double)y[i] - my;
+    cxy += dp * dy;
     cxx += dp * dp;
+    cyy += dy * dy;
   }
   for (int o = 16; o > 0; o >>= 1) {
     cxy += __shfl_xor_sync(0xffffffffu, cxy, o);
     cxx += __shfl_xor_sync(0xffffffffu, cxx, o);
+    cyy += __shfl_xor_sync(0xffffffffu, cyy, o);
   }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) { s1[threadIdx.x >> 5] = cxy; s2[threadIdx.x >> 5] = cxx; }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = cxy;
+    s2[threadIdx.x >> 5] = cxx;
+    s3[threadIdx.x >> 5] = cyy;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double txy = 0.0, txx = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { txy += s1[w]; txx += s2[w]; }
+    double txy = 0.0, txx = 0.0, tyy = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { txy += s1[w]; txx += s2[w]; tyy += s3[w]; }
     double a = txx > 0.0 ? txy / txx : 0.0;
     a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+    if (shrink) a *= (txx > 0.0 && tyy > 0.0) ? (txy * txy) / (txx * tyy) : 0.0;
     out[0] = (float)a;
   }
 }
@@ -489,13 +498,13 @@ fa_status fa_gnn_warm_start(int32_t n, const float* log_v1, const float* pred, f
 }
 
 fa_status fa_gnn_fit_scale(int32_t n, const float* pred, const float* y, float max_abs,
-                           float* scale, fa_stream_t stream) {
+                           int32_t shrink, float* scale, fa_stream_t stream) {
   if (n < 1 || !pred || !y || !scale || !(max_abs > 0.f)) {
     set_error("fa_gnn_fit_scale: bad argument");
     return FA_ERR_ARG;
   }
   k_gnn_fit_scale<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(n, pred, y, max_abs,
-                                                                          scale);
+                                                                          shrink, scale);
   FA_LAUNCHED("k_gnn_fit_scale");
   return FA_OK;
 }

@@ -125,6 +125,7 @@ class WarmStarter:
 
     MAX_CORR = 20.0     # bound on a predicted change of the correction (log units)
     CALIBRATE = True    # fit the trust alpha after every solve (False: alpha = 1)
+    SHRINK = True       # alpha times the squared correlation of prediction and change
 
     def __init__(self, aligner: api.Aligner, mode: str = "learned",
                  model: WarmStartModel | None = None, anchors=None):
@@ -180,7 +181,8 @@ class WarmStarter:
             # against the prediction: the next solve's trust alpha
             L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, -1.0, self.log_v1, self.change)
             L.fa_vec_axpby(self.al.n2, 1.0, self.change, -1.0, self.corr, self.change)
-            L.fa_gnn_fit_scale(self.al.n2, self.pred, self.change, self.MAX_CORR, self.alpha)
+            L.fa_gnn_fit_scale(self.al.n2, self.pred, self.change, self.MAX_CORR, self.alpha,
+                               shrink=self.SHRINK)
             self.predicted = False
         L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, -1.0, self.log_v1, self.corr)
         L.fa_vec_axpby(self.al.n2, 1.0, self.al.log_v, 0.0, None, self.pot)

@@ -179,9 +179,11 @@ def test_fit_scale_matches_oracle():
     pred = (3.0 * rng.standard_normal(n)).astype(np.float32)
     pred[7] = np.inf
     for k in (0.3, 1.7, -0.4):
-        y = (k * np.clip(pred, -2.0, 2.0) * np.isfinite(pred) + 0.1 * rng.standard_normal(n)
+        y = (k * np.clip(pred, -2.0, 2.0) * np.isfinite(pred) + 0.7 * rng.standard_normal(n)
              + 5.0).astype(np.float32)
-        out = torch.zeros(1, device="cuda")
-        L.fa_gnn_fit_scale(n, torch.from_numpy(pred).cuda(), torch.from_numpy(y).cuda(), 2.0, out)
-        want = G.fit_scale(pred.astype(np.float64), y.astype(np.float64), 2.0)
-        assert abs(out.item() - want) <= 1e-6, (k, out.item(), want)
+        for shrink in (False, True):
+            out = torch.zeros(1, device="cuda")
+            L.fa_gnn_fit_scale(n, torch.from_numpy(pred).cuda(), torch.from_numpy(y).cuda(), 2.0,
+                               out, shrink=shrink)
+            want = G.fit_scale(pred.astype(np.float64), y.astype(np.float64), 2.0, shrink=shrink)
+            assert abs(out.item() - want) <= 1e-6, (k, shrink, out.item(), want)

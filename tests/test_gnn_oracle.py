@@ -93,3 +93,15 @@ def test_fit_scale_hand_values():
     want = G.fit_scale(np.array([1.0, 0.0, 3.0, -1.0]), np.array([0.2, 0.0, 0.6, -0.2]), 20.0)
     assert abs(G.fit_scale(q, np.array([0.2, 0.0, 0.6, -0.2]), 20.0) - want) < 1e-15
     assert abs(want - 0.2) < 1e-15
+
+
+def test_fit_scale_shrink_is_alpha_times_squared_correlation():
+    p = np.array([1.0, 2.0, 3.0, 6.0])
+    noise = np.array([0.3, -0.6, 0.3, 0.0])          # centred, orthogonal to the centred p
+    y = 0.5 * p + noise
+    dp = p - p.mean()
+    rho2 = (dp @ (y - y.mean())) ** 2 / ((dp @ dp) * ((y - y.mean()) @ (y - y.mean())))
+    assert abs(G.fit_scale(p, y, 20.0) - 0.5) < 1e-15
+    assert abs(G.fit_scale(p, y, 20.0, shrink=True) - 0.5 * rho2) < 1e-15
+    assert 0.0 < rho2 < 1.0
+    assert G.fit_scale(p, 0.5 * p, 20.0, shrink=True) == 0.5    # exact fit: rho^2 = 1
