@@ -298,10 +298,10 @@ fa_status fa_gnn_warm_start(int32_t n, const float* log_v1, const float* pred,
  * to predict, clipped to [0, 1]:
  *   p = clamp(pred, -max_abs, max_abs) (non-finite -> 0),
  *   a = clip( sum_j (p_j - mean p)(y_j - mean y) / sum_j (p_j - mean p)^2, 0, 1 )
- * (0 when p is constant); with shrink != 0 the result is a rho^2, rho the
- * correlation of p and y, so a prediction that explains little of y is
- * trusted little.  Centred because potentials are defined up to a
- * constant.  pred, y: device vectors of n floats; scale: device scalar.
+ * (0 when p is constant).  shrink selects a further factor from rho, the
+ * correlation of p and y, so that a prediction that explains little of y
+ * is trusted little: 1 -> a rho^2, 2 -> a |rho|, anything else -> a.
+ * Centred because potentials are defined up to a constant.  pred, y: device vectors of n floats; scale: device scalar.
  * Fixed-order FP64 sums.  Used after each solve to damp the next solve's
  * prediction by how well the last one matched (0: the previous-correction
  * start, 1: the network's own prediction). */

@@ -105,11 +105,12 @@ def features(Abar_deg: np.ndarray, log_v1: np.ndarray, corr_prev: np.ndarray,
                      pp - pp.mean(), am, np.full(n, np.log1p(outer_index))], axis=1)
 
 
-def fit_scale(pred: np.ndarray, y: np.ndarray, max_abs: float, shrink: bool = False) -> float:
+def fit_scale(pred: np.ndarray, y: np.ndarray, max_abs: float, shrink: int = 0) -> float:
     """The trust in a prediction: the least-squares scale alpha minimising
     |(y - mean y) - alpha (p - mean p)|^2 for p = clamp(pred, -max_abs,
     max_abs) (non-finite entries 0), clipped to [0, 1]; 0 when p is
-    constant.  shrink: alpha times the squared correlation of p and y."""
+    constant.  shrink 1: alpha times the squared correlation rho^2 of p and
+    y; shrink 2: alpha times |rho|; 0 (or any other value): alpha alone."""
     p = np.where(np.isfinite(pred), np.clip(np.asarray(pred, np.float64), -max_abs, max_abs), 0.0)
     yy = np.asarray(y, np.float64)
     dp, dy = p - p.mean(), yy - yy.mean()
@@ -117,7 +118,10 @@ def fit_scale(pred: np.ndarray, y: np.ndarray, max_abs: float, shrink: bool = Fa
     if den == 0.0:
         return 0.0
     a = float(min(1.0, max(0.0, (dp @ dy) / den)))
-    if shrink:
-        vy = float(dy @ dy)
-        a *= float((dp @ dy) ** 2 / (den * vy)) if vy > 0.0 else 0.0
+    vy = float(dy @ dy)
+    r2 = float((dp @ dy) ** 2 / (den * vy)) if vy > 0.0 else 0.0
+    if int(shrink) == 1:
+        a *= r2
+    elif int(shrink) == 2:
+        a *= float(np.sqrt(r2))
     return a

@@ -357,8 +357,8 @@ def fa_gnn_warm_start(n, log_v1, pred, max_abs, out, scale=None, stream=None) ->
                                    ptr(out), stream_ptr(stream)), "fa_gnn_warm_start")
 
 
-def fa_gnn_fit_scale(n, pred, y, max_abs, scale, shrink=False, stream=None) -> None:
-    _check(lib().fa_gnn_fit_scale(int(n), ptr(pred), ptr(y), float(max_abs), 1 if shrink else 0,
+def fa_gnn_fit_scale(n, pred, y, max_abs, scale, shrink=0, stream=None) -> None:
+    _check(lib().fa_gnn_fit_scale(int(n), ptr(pred), ptr(y), float(max_abs), int(shrink),
                                   ptr(scale), stream_ptr(stream)), "fa_gnn_fit_scale")
 
 

@@ -335,7 +335,9 @@ __global__ void __launch_bounds__(1024) k_gnn_fit_scale(int n, const float* __re
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { txy += s1[w]; txx += s2[w]; tyy += s3[w]; }
     double a = txx > 0.0 ? txy / txx : 0.0;
     a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
-    if (shrink) a *= (txx > 0.0 && tyy > 0.0) ? (txy * txy) / (txx * tyy) : 0.0;
+    const double r2 = (txx > 0.0 && tyy > 0.0) ? (txy * txy) / (txx * tyy) : 0.0;
+    if (shrink == 1) a *= r2;
+    else if (shrink == 2) a *= sqrt(r2);
     out[0] = (float)a;
   }
 }

@@ -125,7 +125,7 @@ class WarmStarter:
 
     MAX_CORR = 20.0     # bound on a predicted change of the correction (log units)
     CALIBRATE = True    # fit the trust alpha after every solve (False: alpha = 1)
-    SHRINK = True       # alpha times the squared correlation of prediction and change
+    SHRINK = 2          # alpha times |rho| of prediction and change (1: rho^2, 0: alpha alone)
 
     def __init__(self, aligner: api.Aligner, mode: str = "learned",
                  model: WarmStartModel | None = None, anchors=None):

@@ -181,7 +181,7 @@ def test_fit_scale_matches_oracle():
     for k in (0.3, 1.7, -0.4):
         y = (k * np.clip(pred, -2.0, 2.0) * np.isfinite(pred) + 0.7 * rng.standard_normal(n)
              + 5.0).astype(np.float32)
-        for shrink in (False, True):
+        for shrink in (0, 1, 2):
             out = torch.zeros(1, device="cuda")
             L.fa_gnn_fit_scale(n, torch.from_numpy(pred).cuda(), torch.from_numpy(y).cuda(), 2.0,
                                out, shrink=shrink)

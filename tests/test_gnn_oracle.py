@@ -95,13 +95,18 @@ def test_fit_scale_hand_values():
     assert abs(want - 0.2) < 1e-15
 
 
-def test_fit_scale_shrink_is_alpha_times_squared_correlation():
+def test_fit_scale_shrink_is_alpha_times_a_power_of_the_correlation():
     p = np.array([1.0, 2.0, 3.0, 6.0])
     noise = np.array([0.3, -0.6, 0.3, 0.0])          # centred, orthogonal to the centred p
     y = 0.5 * p + noise
     dp = p - p.mean()
     rho2 = (dp @ (y - y.mean())) ** 2 / ((dp @ dp) * ((y - y.mean()) @ (y - y.mean())))
     assert abs(G.fit_scale(p, y, 20.0) - 0.5) < 1e-15
-    assert abs(G.fit_scale(p, y, 20.0, shrink=True) - 0.5 * rho2) < 1e-15
+    assert abs(G.fit_scale(p, y, 20.0, shrink=1) - 0.5 * rho2) < 1e-15
+    assert abs(G.fit_scale(p, y, 20.0, shrink=2) - 0.5 * np.sqrt(rho2)) < 1e-15
     assert 0.0 < rho2 < 1.0
-    assert G.fit_scale(p, 0.5 * p, 20.0, shrink=True) == 0.5    # exact fit: rho^2 = 1
+    # hand value: dp = (-2, -1, 0, 3), dp.dp = 14, dy = 0.5 dp + noise,
+    # dy.dy = 3.5 + 0.54 = 4.04, (dp.dy)^2 = 49, rho^2 = 49 / (14 * 4.04)
+    assert abs(rho2 - 49.0 / (14.0 * 4.04)) < 1e-14
+    for mode in (1, 2):
+        assert G.fit_scale(p, 0.5 * p, 20.0, shrink=mode) == 0.5   # exact fit: rho^2 = 1
