@@ -416,10 +416,12 @@ fa_status fa_sinkhorn_shard_cols(fa_ctx* ctx, const void* K, const float* log_u,
  * sweep (Algorithm 1, Phase 3) on n1 rows of ld columns (ld a positive multiple
  * of 128) in storage type dtype, from host logic only (no device query;
  * the FA_SWEEP_* tuning variables apply).  out (host int32[8]) receives:
- * cluster size Q, slab width W = ld / Q (elements), 16-byte vectors per
- * thread per row S, rows per step R, ring stages NS, threads per CTA NT,
- * kind (0 CTA-synchronous, 1 warp-specialised), and the cluster count G
- * before the device's occupancy limit is applied.
+ * cluster size Q, the widest slab W (elements; the row's 16-byte units are
+ * split over the Q CTAs as evenly as possible, so slabs differ by at most
+ * one unit), 16-byte vectors per thread per row S, rows per step R, ring
+ * stages NS, threads per CTA NT, kind (0 CTA-synchronous, 1 warp-
+ * specialised, 2 tensor-core row pass), and the cluster count G before the
+ * device's occupancy limit is applied.
  * FA_ERR_UNSUPPORTED when no shape fits a row that wide.
  * -------------------------------------------------------------------- */
 fa_status fa_sweep_plan(int32_t n1, int64_t ld, int32_t dtype, int32_t* out);

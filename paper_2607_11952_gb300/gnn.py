@@ -224,7 +224,7 @@ class WarmStarter:
 @dataclasses.dataclass
 class Sample:
     graph: api.Graph          # column graph G2 (kept alive)
-    F: torch.Tensor           # n x 3 features
+    F: torch.Tensor           # n x FIN features
     y: torch.Tensor           # n targets: change of the correction, c - c_prev
 
 

@@ -2,7 +2,7 @@
 compare it with the cold start on a larger pair.
 
   python -m paper_2607_11952_gb300.train_warmstart [--pairs 67 --outer 30
-        --epochs 15 --eval-n 20000 --out paper_2607_11952_gb300/gnn_weights.json]
+        --epochs 20 --eval-n 20000 --out paper_2607_11952_gb300/gnn_weights.json]
 
 Training pairs: Chung-Lu, n ~ U[2000, 5000], exponent ~ U[2.1, 2.8], edge
 noise ~ U[5%, 20%], 64-dim attributes; one sample per outer iteration
@@ -72,7 +72,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--pairs", type=int, default=67)
     ap.add_argument("--outer", type=int, default=30)
-    ap.add_argument("--epochs", type=int, default=15)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--eval-n", type=int, default=20000)
