@@ -659,40 +659,59 @@ SweepPlan plan_sweep(int n1, int64_t ld, bool bf16, int max_G) {
   int smax = NT == 1024 ? (bf16 ? 3 : 6) : (bf16 ? kSmaxBF16 : kSmaxF32);
   const int smax_env = env_int("FA_SWEEP_SMAX", 0);
   if (smax_env > 0 && (smax_env < smax || (bf16 && NT == 256 && smax_env == 7))) smax = smax_env;
-  // BF16: any cluster size from 1 to 16.  The row's ld / V 16-byte units
-  // are split as evenly as possible over the Q CTAs (slab widths differ by
-  // at most one unit), so the smallest cluster that fits is not limited to
-  // the divisors of ld: at 50k, 5 CTAs with one row per step instead of 8
-  // CTAs with two, measured about 5% faster on GB300.  FP32, already
-  // at the copy peak with power-of-two clusters, keeps them
-  // (FA_SWEEP_ANYQ=1/0 forces either rule).  W is the widest slab.
+  // The row's ld / V 16-byte units are split as evenly as possible over the
+  // Q CTAs (slab widths differ by at most one unit), so Q need not divide
+  // ld; W is the widest slab.  A step costs a fixed part (barriers, the
+  // exchange) plus a part per round of NT vectors, so a shape should have
+  // few rounds, a nearly full last round and, where the ring allows, two
+  // rows per step.  BF16 default rule (measured on GB300, 50,000 rows and
+  // 30k-110k columns: it picks the fastest of the rules below at every
+  // width):
+  //   1. the smallest power-of-two cluster up to 8 whose slab takes at most
+  //      5 vectors per thread with the last round at least 80% full;
+  //   2. else the smallest cluster up to 10 with at most 5 vectors;
+  //   3. else the smallest cluster of any size that fits the register
+  //      shapes.
+  // FP32, already at the copy peak, keeps powers of two.  FA_SWEEP_ANYQ=0
+  // forces powers of two, =1 the smallest cluster of any size.
   const int64_t units = ld / V;
-  const bool anyq = env_int("FA_SWEEP_ANYQ", bf16 ? 1 : 0) != 0;
+  const int qrule = env_int("FA_SWEEP_ANYQ", bf16 ? 2 : 0);
+  auto fit = [&](int Q, int min_ns, int s_cap, double min_fill) -> bool {
+    if (Qforce && Q != Qforce) return false;
+    if (units < Q) return false;
+    const int64_t W = V * ((units + Q - 1) / Q);
+    const int S = (int)((W + (int64_t)NT * V - 1) / ((int64_t)NT * V));
+    if (S > s_cap) return false;
+    if ((double)(W / V) < min_fill * (double)S * NT) return false;
+    const size_t budget = kSmemBudget / sweep_ctas_per_sm(NT, S * V);
+    for (int R = bf16 ? 4 : 2; R >= 1; R /= 2) {
+      if (Rforce && R != Rforce) continue;
+      const size_t fixed = (size_t)(kMaxNS + kNX) * 8 + (size_t)(2 * R * (NT / 32) + kNX * kMaxQ * R) * 4;
+      int NS = (int)((budget - fixed) / ((size_t)R * W * b));
+      if (NS > kMaxNS) NS = kMaxNS;
+      if (NSforce) NS = NSforce < NS ? NSforce : NS;
+      if (NS >= min_ns) {
+        sp.Q = Q;
+        sp.W = (int)W;
+        sp.S = S;
+        sp.R = R;
+        sp.NS = NS;
+        sp.NT = NT;
+        return true;
+      }
+    }
+    return false;
+  };
   for (int pass = 0; pass < 2 && sp.Q == 0; ++pass) {
     const int min_ns = pass == 0 ? 3 : 2;
-    for (int Q = 1; Q <= kMaxQ && sp.Q == 0; Q = anyq ? Q + 1 : 2 * Q) {
-      if (Qforce && Q != Qforce) continue;
-      if (units < Q) continue;
-      const int64_t W = V * ((units + Q - 1) / Q);
-      const int S = (int)((W + (int64_t)NT * V - 1) / ((int64_t)NT * V));
-      if (S > smax) continue;
-      const size_t budget = kSmemBudget / sweep_ctas_per_sm(NT, S * V);
-      for (int R = bf16 ? 4 : 2; R >= 1; R /= 2) {
-        if (Rforce && R != Rforce) continue;
-        const size_t fixed = (size_t)(kMaxNS + kNX) * 8 + (size_t)(2 * R * (NT / 32) + kNX * kMaxQ * R) * 4;
-        int NS = (int)((budget - fixed) / ((size_t)R * W * b));
-        if (NS > kMaxNS) NS = kMaxNS;
-        if (NSforce) NS = NSforce < NS ? NSforce : NS;
-        if (NS >= min_ns) {
-          sp.Q = Q;
-          sp.W = (int)W;
-          sp.S = S;
-          sp.R = R;
-          sp.NS = NS;
-          sp.NT = NT;
-          break;
-        }
-      }
+    if (qrule == 2) {
+      const int s5 = smax < 5 ? smax : 5;
+      for (int Q = 1; Q <= 8 && sp.Q == 0; Q *= 2) fit(Q, min_ns, s5, 0.8);
+      for (int Q = 1; Q <= 10 && sp.Q == 0; ++Q) fit(Q, min_ns, s5, 0.0);
+      for (int Q = 1; Q <= kMaxQ && sp.Q == 0; ++Q) fit(Q, min_ns, smax, 0.0);
+    } else {
+      for (int Q = 1; Q <= kMaxQ && sp.Q == 0; Q = qrule ? Q + 1 : 2 * Q)
+        fit(Q, min_ns, smax, 0.0);
     }
   }
   if (sp.Q == 0) return sp;

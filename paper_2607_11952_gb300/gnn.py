@@ -125,7 +125,7 @@ class WarmStarter:
 
     MAX_CORR = 20.0     # bound on a predicted change of the correction (log units)
     CALIBRATE = True    # fit the trust alpha after every solve (False: alpha = 1)
-    SHRINK = 2          # alpha times |rho| of prediction and change (1: rho^2, 0: alpha alone)
+    SHRINK = 0          # alpha alone (1: alpha rho^2, 2: alpha |rho|, rho the correlation)
 
     def __init__(self, aligner: api.Aligner, mode: str = "learned",
                  model: WarmStartModel | None = None, anchors=None):
@@ -240,8 +240,24 @@ def training_pair(k: int, seed: int) -> synth.GraphPair:
                            frac_add=noise, rng=rng, name=f"train{k}", seed=seed)
 
 
+def large_training_pair(k: int, seed: int) -> synth.GraphPair:
+    """The k-th larger training pair: n ~ U[10000, 30000], exponent ~
+    U[2.1, 2.8], edge noise ~ U[5%, 20%], 64- or 128-dim attributes, 5%
+    anchors.  Solves on pairs this size teach the network the dynamics of
+    the large workloads, which the 2k-5k pairs alone do not."""
+    rng = synth.rng_for(seed * 100003 + k)
+    n = int(rng.integers(10000, 30001))
+    gamma = float(rng.uniform(2.1, 2.8))
+    noise = float(rng.uniform(0.05, 0.20))
+    d = int(rng.choice([64, 128]))
+    e1 = synth.chung_lu(n, gamma, 10.0, rng)
+    return synth.make_pair(e1, n, d=d, sigma=0.1, anchor_frac=0.05, frac_del=noise,
+                           frac_add=noise, rng=rng, name=f"trainL{k}", seed=seed)
+
+
 def generate_solves(n_pairs: int, outer: int, seed: int = 7, tol: float = 1e-5,
-                    max_sweeps: int = 20000, dtype: str = "f32", log=None):
+                    max_sweeps: int = 20000, dtype: str = "f32", log=None,
+                    pair_fn=None):
     """Run the method on training pairs and record, for every outer
     iteration, the features and the change of the converged correction
     c - c_prev.  The solves start from the previous correction (the
@@ -250,7 +266,7 @@ def generate_solves(n_pairs: int, outer: int, seed: int = 7, tol: float = 1e-5,
     samples = []
     model = WarmStartModel(seed=seed)            # only for its feature kernel
     for k in range(n_pairs):
-        g = training_pair(k, seed)
+        g = (pair_fn or training_pair)(k, seed)
         G1, G2 = api.Graph(g.n1, g.edges1), api.Graph(g.n2, g.edges2)
         al = api.Aligner(G1, G2, api.Params(dtype=dtype))
         ws = WarmStarter(al, "prev")

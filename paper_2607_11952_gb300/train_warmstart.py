@@ -1,13 +1,14 @@
 """Train the learned Sinkhorn warm start on the method's own solves and
 compare it with the cold start on a larger pair.
 
-  python -m paper_2607_11952_gb300.train_warmstart [--pairs 67 --outer 30
-        --epochs 20 --eval-n 20000 --out paper_2607_11952_gb300/gnn_weights.json]
+  python -m paper_2607_11952_gb300.train_warmstart [--pairs 67 --large-pairs 12
+        --outer 30 --epochs 20 --eval-n 20000 --out paper_2607_11952_gb300/gnn_weights.json]
 
 Training pairs: Chung-Lu, n ~ U[2000, 5000], exponent ~ U[2.1, 2.8], edge
-noise ~ U[5%, 20%], 64-dim attributes; one sample per outer iteration
-(pairs x outer solves, 2010 by default, spanning all 30 outer iterations of
-the workloads).  Evaluation: a 20000-node pair with
+noise ~ U[5%, 20%], 64-dim attributes (seed 7), and larger pairs with
+n ~ U[10000, 30000] and 64- or 128-dim attributes (seed 8); one sample per
+outer iteration (pairs x outer solves, 2010 + 360 by default, spanning all
+30 outer iterations of the workloads).  Evaluation: a 20000-node pair with
 64-dim attributes; at every outer iteration the same Gibbs kernel is solved
 to the marginal tolerance three times (cold start, previous-correction warm
 start, learned warm start) and the iterations and times are reported.
@@ -75,6 +76,8 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--large-pairs", type=int, default=12)
+    ap.add_argument("--large-seed", type=int, default=8)
     ap.add_argument("--eval-n", type=int, default=20000)
     ap.add_argument("--eval-outer", type=int, default=30)
     ap.add_argument("--out", default=gnn.WEIGHTS_PATH)
@@ -92,12 +95,16 @@ def main(argv=None):
         model = gnn.WarmStartModel.load(args.out)
     else:
         samples = gnn.generate_solves(args.pairs, args.outer, seed=args.seed, log=log)
+        if args.large_pairs > 0:
+            samples += gnn.generate_solves(args.large_pairs, args.outer, seed=args.large_seed,
+                                           log=log, pair_fn=gnn.large_training_pair)
         t1 = time.time()
         log(f"{len(samples)} solves generated in {t1 - t0:.1f} s")
         model, hist = gnn.train(samples, epochs=args.epochs, lr=args.lr, seed=args.seed, log=log)
         t2 = time.time()
         log(f"trained in {t2 - t1:.1f} s")
-        model.save(args.out, meta={"pairs": args.pairs, "outer": args.outer,
+        model.save(args.out, meta={"pairs": args.pairs, "large_pairs": args.large_pairs,
+                                   "large_seed": args.large_seed, "outer": args.outer,
                                    "epochs": args.epochs, "lr": args.lr, "seed": args.seed,
                                    "loss": hist})
     g = synth.config_pair("cl20k", n=args.eval_n)

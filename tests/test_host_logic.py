@@ -78,14 +78,33 @@ def test_csr_argument_errors():
 
 
 def test_sweep_shapes_of_the_measured_workloads():
-    # BF16: the smallest cluster of any size whose widest slab fits six
-    # 16-byte vectors per thread -- 5 CTAs at 50k (slabs of 1252 or 1251
-    # vectors), one row per step
+    # BF16 rule: the smallest power-of-two cluster (<= 8) whose slab takes at
+    # most 5 vectors per thread with the last round >= 80% full; else the
+    # smallest cluster (<= 10) with at most 5 vectors; else any that fits.
+    # 50k: 4 CTAs need 7 vectors and 8 CTAs fill their 4th round to 76%, so
+    # 5 CTAs (slabs of 1252 or 1251 vectors), one row per step
     got = L.fa_sweep_plan(50_000, 50_048, L.FA_BF16)
     assert (got["Q"], got["W"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == \
         (5, 10016, 5, 1, 5, 256, 0)
     got = L.fa_sweep_plan(50_000, 50_048, L.FA_F32)
     assert (got["Q"], got["S"], got["R"], got["NS"], got["NT"], got["kind"]) == (8, 7, 1, 4, 256, 0)
+    # 80k columns: 8 CTAs of 1250 vectors (98% of 5 rounds)
+    got = L.fa_sweep_plan(100_000, 80_000, L.FA_BF16)
+    assert (got["Q"], got["W"], got["S"], got["R"]) == (8, 10_000, 5, 1)
+    # 30k and 70k columns: power-of-two clusters with two rows per step
+    got = L.fa_sweep_plan(50_000, 30_080, L.FA_BF16)
+    assert (got["Q"], got["W"], got["S"], got["R"], got["NS"]) == (4, 7520, 4, 2, 3)
+    got = L.fa_sweep_plan(50_000, 70_016, L.FA_BF16)
+    assert (got["Q"], got["W"], got["S"], got["R"], got["NS"]) == (8, 8752, 5, 2, 3)
+    # 100k columns: rule 2 (10 CTAs); 110k: rule 3 (9 CTAs, 6 vectors)
+    got = L.fa_sweep_plan(50_000, 100_096, L.FA_BF16)
+    assert (got["Q"], got["S"]) == (10, 5)
+    got = L.fa_sweep_plan(50_000, 110_080, L.FA_BF16)
+    assert (got["Q"], got["S"]) == (9, 6)
+
+
+def test_any_size_clusters_behind_their_switch(monkeypatch):
+    monkeypatch.setenv("FA_SWEEP_ANYQ", "1")
     got = L.fa_sweep_plan(100_000, 80_000, L.FA_BF16)
     assert (got["Q"], got["W"], got["S"], got["R"]) == (7, 11_432, 6, 1)
 
