@@ -204,7 +204,7 @@ def run_ours(args):
     algo_bytes = g.n1 * g.n2 * bpe
     peak, peak_kind = _peaks()
     achieved = algo_bytes / (avg_sweep * 1e-3) / 1e9 if avg_sweep > 0 else None
-    traffic = _ncu_traffic(args)
+    traffic = _ncu_traffic(args, g.n1, g.n2)
 
     def timed_alignment(dtype, warm, runs=1):
         """The step on a fresh aligner of the given storage type and warm
@@ -302,9 +302,11 @@ def sweep_source_hash():
     return h.hexdigest()
 
 
-def _ncu_traffic(args):
+def _ncu_traffic(args, n1, n2):
     """DRAM bytes per k_sweep launch from the committed ncu summary, if it
-    was taken for the current kernel source and dtype (None otherwise)."""
+    was taken for the current kernel source, dtype and row width, scaled
+    from the captured rows to n1 (None otherwise: another width has another
+    launch shape)."""
     p = os.path.join(ROOT, "profiles", "k_sweep_traffic.json")
     if not os.path.exists(p):
         return None
@@ -312,7 +314,9 @@ def _ncu_traffic(args):
     if d.get("source_sha256") != sweep_source_hash():
         return None
     e = d.get(args.dtype)
-    return e.get("dram_bytes_per_launch_full_size") if e else None
+    if not e or e.get("captured_n2") != n2:
+        return None
+    return int(round(e["dram_bytes_per_launch_captured"] * n1 / e["captured_n1"]))
 
 
 def _e2e(args, g, dev, api, model):
