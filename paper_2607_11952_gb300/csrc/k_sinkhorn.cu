@@ -821,11 +821,17 @@ int sweep_max_active_clusters(const SweepPlan& sp, bool bf16) {
 }
 
 // ------------------------------------------------------------ finalize
-// colsum_j = sum_g colpart[g][j] (fixed order), column marginal
-// m_j = v_j colsum_j, err = sum_j |m_j - nu| in FP64 (deterministic two-level
-// reduction: per-block partials, summed in index order by the last block),
-// and the next column scaling log v_j = log nu - log colsum_j.
+// colsum_j = sum_g colpart[g][j] (in the order g = 0, 1, ..., G-1), column
+// marginal m_j = v_j colsum_j, err = sum_j |m_j - nu| in FP64 (deterministic
+// two-level reduction: per-block partials, summed by the last block in a
+// fixed order), and the next column scaling log v_j = log nu - log colsum_j.
+// Four columns per thread: colpart rows are read as 16-byte vectors (ld and
+// the column offsets passed in are multiples of 4); the log_v arrays are
+// read and written element by element (no alignment assumed).  v_j enters
+// the error through expf widened to FP64: the FP32 column sums already
+// carry a relative error of about G 2^-24, far above expf's.
 constexpr int kFinThreads = 256;
+constexpr int kFinCols = 4;
 
 __global__ void __launch_bounds__(kFinThreads) k_col_finalize(
     int n2, int64_t ld, int G, const float* __restrict__ colpart,
@@ -835,23 +841,45 @@ __global__ void __launch_bounds__(kFinThreads) k_col_finalize(
     int* __restrict__ status) {
   __shared__ double sred[kFinThreads / 32];
   __shared__ bool last;
-  const int j = blockIdx.x * kFinThreads + threadIdx.x;
+  const int j = (blockIdx.x * kFinThreads + threadIdx.x) * kFinCols;
   double e = 0.0;
   if (j < n2) {
-    float cs = 0.f;
-    for (int g = 0; g < G; ++g) cs += colpart[(int64_t)g * ld + j];
-    if (log_v_cur) {
-      const double m = exp((double)log_v_cur[j]) * (double)cs;
-      e = fabs(m - (double)nu);
+    const float* p = colpart + j;
+    float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+    int g = 0;
+    for (; g + 4 <= G; g += 4) {   // four rows in flight, added in row order
+      const float4 a0 = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)g * ld));
+      const float4 a1 = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)(g + 1) * ld));
+      const float4 a2 = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)(g + 2) * ld));
+      const float4 a3 = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)(g + 3) * ld));
+      cs.x += a0.x; cs.y += a0.y; cs.z += a0.z; cs.w += a0.w;
+      cs.x += a1.x; cs.y += a1.y; cs.z += a1.z; cs.w += a1.w;
+      cs.x += a2.x; cs.y += a2.y; cs.z += a2.z; cs.w += a2.w;
+      cs.x += a3.x; cs.y += a3.y; cs.z += a3.z; cs.w += a3.w;
     }
-    float lv;
-    if (cs > 0.f && isfinite(cs)) {
-      lv = log_nu - logf(cs);
-    } else {
-      atomicOr(status, ST_NUMERIC);
-      lv = log_nu + 87.0f;   // keep finite; the status word reports it
+    for (; g < G; ++g) {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)g * ld));
+      cs.x += a.x; cs.y += a.y; cs.z += a.z; cs.w += a.w;
     }
-    log_v_next[j] = lv;
+    const float c4[kFinCols] = {cs.x, cs.y, cs.z, cs.w};
+#pragma unroll
+    for (int k = 0; k < kFinCols; ++k) {
+      const int jj = j + k;
+      if (jj >= n2) break;
+      const float c = c4[k];
+      if (log_v_cur) {
+        const double m = (double)expf(log_v_cur[jj]) * (double)c;
+        e += fabs(m - (double)nu);
+      }
+      float lv;
+      if (c > 0.f && isfinite(c)) {
+        lv = log_nu - logf(c);
+      } else {
+        atomicOr(status, ST_NUMERIC);
+        lv = log_nu + 87.0f;   // keep finite; the status word reports it
+      }
+      log_v_next[jj] = lv;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
   if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = e;
@@ -865,14 +893,29 @@ __global__ void __launch_bounds__(kFinThreads) k_col_finalize(
     last = (prev == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
+    // the last block sums the block partials: thread t takes blocks t,
+    // t + 256, ... in order, then a fixed tree
     __threadfence();
     double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b)
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kFinThreads)
       t += ((volatile double*)err_part)[b];
-    *err_out = t;
-    *ticket = 0u;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double u = 0.0;
+      for (int w = 0; w < kFinThreads / 32; ++w) u += sred[w];
+      *err_out = u;
+      *ticket = 0u;
+    }
   }
+}
+
+int col_finalize_blocks(int n2) {
+  const int per = kFinThreads * kFinCols;
+  return (n2 + per - 1) / per;
 }
 
 fa_status launch_col_finalize(int n2, int64_t ld, int G, const float* colpart,
@@ -880,7 +923,11 @@ fa_status launch_col_finalize(int n2, int64_t ld, int G, const float* colpart,
                               float* log_v_next, double* err_part,
                               unsigned* ticket, double* err_out, int* status,
                               cudaStream_t s) {
-  const int blocks = (n2 + kFinThreads - 1) / kFinThreads;
+  if ((reinterpret_cast<uintptr_t>(colpart) & 15u) != 0 || (ld & 3) != 0) {
+    set_error("column finalisation: partial sums not 16-byte aligned");
+    return FA_ERR_ARG;
+  }
+  const int blocks = col_finalize_blocks(n2);
   k_col_finalize<<<blocks, kFinThreads, 0, s>>>(
       n2, ld, G, colpart, log_v_cur, nu, logf(nu), log_v_next, err_part,
       ticket, err_out, status);

@@ -365,21 +365,18 @@ __global__ void __launch_bounds__(256) k_spmm_left_T(
   }
 }
 
-// Row-per-warp form of the left SpMM: tile 32 rows x 64 columns, warp w
-// owns rows 4w..4w+3 (lane l: columns 2l, 2l+1), four neighbour gathers in
-// flight, transposed store through shared memory.  Used for Pass A's two
-// value sets; FA_PASSA_ROWS=0/1 forces either form.
 template <int NV> struct VecF;
 template <> struct VecF<1> { using T = float; };
 template <> struct VecF<2> { using T = float2; };
 
-__device__ __forceinline__ float2 load_pair(const float* p) {
-  return __ldg(reinterpret_cast<const float2*>(p));
-}
-__device__ __forceinline__ float2 load_pair(const __nv_bfloat16* p) {
-  __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
-  return __bfloat1622float2(v);
-}
+// Row form of the left product, transposed store: CTA tile of 32 rows i by
+// 128 columns j; warp per row (4 rows per warp in turn), lane l covers
+// columns 4l .. 4l+3 of the tile, and kRowGathers neighbour rows
+// D[k, j0:j0+128] are in flight per warp (8 B per lane and gather in BF16,
+// 16 B in FP32).  Each output sums its row's edges in CSR order, so the
+// result does not depend on the tile shape.  Used for Pass A's two value
+// sets; FA_PASSA_ROWS=1 selects it for one value set too.
+constexpr int kRowGathers = 8;
 
 template <typename TD, int NV>
 __global__ void __launch_bounds__(256) k_spmm_left_T_rows(
@@ -387,66 +384,66 @@ __global__ void __launch_bounds__(256) k_spmm_left_T_rows(
     const int32_t* __restrict__ ci, const float* __restrict__ va,
     const float* __restrict__ vb, const float* __restrict__ scale,
     const TD* __restrict__ D, float* __restrict__ Wt) {
-  constexpr int TI = 32, TJ = 64, PAD = (NV == 1) ? 1 : 2;
+  constexpr int TI = 32, TJ = 128, PAD = (NV == 1) ? 1 : 2, NG = kRowGathers;
   __shared__ float tile[TI][TJ * NV + PAD];
   const int i0 = blockIdx.x * TI;
   const int j0 = blockIdx.y * TJ;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const TD* dcol = D + j0 + 2 * lane;
-#pragma unroll
+  const TD* dcol = D + j0 + 4 * lane;
+#pragma unroll 1
   for (int rr = 0; rr < 4; ++rr) {
     const int r = warp * 4 + rr;
     const int i = i0 + r;
-    float a0[NV], a1[NV];
+    float acc[4][NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) a0[v] = a1[v] = 0.f;
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[c][v] = 0.f;
     if (i < n1) {
       const int e0 = rp[i], e1 = rp[i + 1];
       int e = e0;
-      // four neighbour gathers in flight
-      for (; e + 4 <= e1; e += 4) {
-        int k[4];
-        float2 d[4];
-        float w[4], x[4];
+      for (; e + NG <= e1; e += NG) {
+        int k[NG];
+        float4 d[NG];
+        float w[NG], x[NG];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) k[u] = ci[e + u];
+        for (int u = 0; u < NG; ++u) k[u] = ci[e + u];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) d[u] = load_pair(dcol + (int64_t)k[u] * ldd);
+        for (int u = 0; u < NG; ++u) d[u] = load_quad(dcol + (int64_t)k[u] * ldd);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < NG; ++u) {
           const float su = scale ? scale[k[u]] : 1.f;
           w[u] = va[e + u] * su;
           x[u] = NV == 2 ? vb[e + u] * su : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          a0[0] = fmaf(w[u], d[u].x, a0[0]);
-          a1[0] = fmaf(w[u], d[u].y, a1[0]);
-          if (NV == 2) {
-            a0[NV - 1] = fmaf(x[u], d[u].x, a0[NV - 1]);
-            a1[NV - 1] = fmaf(x[u], d[u].y, a1[NV - 1]);
+        for (int u = 0; u < NG; ++u) {
+          const float dv[4] = {d[u].x, d[u].y, d[u].z, d[u].w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            acc[c][0] = fmaf(w[u], dv[c], acc[c][0]);
+            if (NV == 2) acc[c][NV - 1] = fmaf(x[u], dv[c], acc[c][NV - 1]);
           }
         }
       }
       for (; e < e1; ++e) {
         const int k0 = ci[e];
-        float s0 = scale ? scale[k0] : 1.f;
-        const float2 d0 = load_pair(dcol + (int64_t)k0 * ldd);
-        float w0 = va[e] * s0;
-        a0[0] = fmaf(w0, d0.x, a0[0]);
-        a1[0] = fmaf(w0, d0.y, a1[0]);
-        if (NV == 2) {
-          float x0 = vb[e] * s0;
-          a0[NV - 1] = fmaf(x0, d0.x, a0[NV - 1]);
-          a1[NV - 1] = fmaf(x0, d0.y, a1[NV - 1]);
+        const float s0 = scale ? scale[k0] : 1.f;
+        const float4 d0 = load_quad(dcol + (int64_t)k0 * ldd);
+        const float dv[4] = {d0.x, d0.y, d0.z, d0.w};
+        const float w0 = va[e] * s0;
+        const float x0 = NV == 2 ? vb[e] * s0 : 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[c][0] = fmaf(w0, dv[c], acc[c][0]);
+          if (NV == 2) acc[c][NV - 1] = fmaf(x0, dv[c], acc[c][NV - 1]);
         }
       }
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      tile[r][(2 * lane) * NV + v] = a0[v];
-      tile[r][(2 * lane + 1) * NV + v] = a1[v];
-    }
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) tile[r][(4 * lane + c) * NV + v] = acc[c][v];
   }
   __syncthreads();
   // transposed store: warp w writes columns c = w, w+8, ...; lane = row
@@ -477,7 +474,7 @@ fa_status launch_spmm_left_T(const DevGraph& g1, int n2, int64_t ldd,
     return v ? atoi(v) : -1;
   }();
   if (form == 1 || two) {
-    dim3 g2d((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 63) / 64));
+    dim3 g2d((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 127) / 128));
     if (d_bf16) {
       auto* Dp = static_cast<const __nv_bfloat16*>(D);
       if (two) k_spmm_left_T_rows<__nv_bfloat16, 2><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
