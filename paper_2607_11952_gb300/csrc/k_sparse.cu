@@ -378,8 +378,8 @@ template <> struct VecF<2> { using T = float2; };
 // sets; FA_PASSA_ROWS=1 selects it for one value set too.
 constexpr int kRowGathers = 8;
 
-template <typename TD, int NV>
-__global__ void __launch_bounds__(256) k_spmm_left_T_rows(
+template <typename TD, int NV, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_spmm_left_T_rows(
     int n1, int n2, int64_t ldd, int64_t ldw, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const float* __restrict__ va,
     const float* __restrict__ vb, const float* __restrict__ scale,
@@ -475,15 +475,24 @@ fa_status launch_spmm_left_T(const DevGraph& g1, int n2, int64_t ldd,
   }();
   if (form == 1 || two) {
     dim3 g2d((unsigned)((g1.n + 31) / 32), (unsigned)((n2 + 127) / 128));
+    // 4 CTAs per SM (64 registers, a 32-byte spill in the BF16 two-set
+    // form) measured 48.7 ms per 50k outer iteration against 49.4 ms for 3
+    // (80 registers); FA_PASSA_MINB=3 selects 3 (tuning)
+    const char* mb = getenv("FA_PASSA_MINB");
+    const bool four = !(mb && atoi(mb) == 3);
+#define FA_PA(T, NVV)                                                                      \
+    if (four) k_spmm_left_T_rows<T, NVV, 4><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, \
+                                                                g1.col, va, vb, scale, Dp, Wt); \
+    else k_spmm_left_T_rows<T, NVV, 3><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr,      \
+                                                           g1.col, va, vb, scale, Dp, Wt);
     if (d_bf16) {
       auto* Dp = static_cast<const __nv_bfloat16*>(D);
-      if (two) k_spmm_left_T_rows<__nv_bfloat16, 2><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
-      else     k_spmm_left_T_rows<__nv_bfloat16, 1><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+      if (two) { FA_PA(__nv_bfloat16, 2) } else { FA_PA(__nv_bfloat16, 1) }
     } else {
       auto* Dp = static_cast<const float*>(D);
-      if (two) k_spmm_left_T_rows<float, 2><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
-      else     k_spmm_left_T_rows<float, 1><<<g2d, 256, 0, s>>>(g1.n, n2, ldd, ldw, g1.row_ptr, g1.col, va, vb, scale, Dp, Wt);
+      if (two) { FA_PA(float, 2) } else { FA_PA(float, 1) }
     }
+#undef FA_PA
     FA_LAUNCHED("k_spmm_left_T_rows");
     return FA_OK;
   }
@@ -591,7 +600,7 @@ __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162flo
 // and the warps of a CTA finish together.  A warp loads 32 edges at a time
 // lane-parallel (column index, both weights times the scaling s_l, and the
 // output column found by binary search in the tile's row pointers), then
-// broadcasts them and keeps kGU gathers of W^T[l, i0:i0+64] (one float4 per
+// broadcasts them and keeps GU gathers of W^T[l, i0:i0+64] (one float4 per
 // lane: rows 2 lane, 2 lane + 1, both value sets) in flight.  The sums are
 // formed without atomics, in a fixed order: a column whose edges lie
 // wholly in one warp's range is stored into the shared tile by that warp;
@@ -607,7 +616,7 @@ constexpr int kCT = 64;    // columns per tile
 
 __device__ __forceinline__ int sw_idx(int r, int c) { return r * kCT + (c ^ (r & 31)); }
 
-template <typename TK, int MINB>
+template <typename TK, int MINB, int GU>
 __global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
     int n1, int n2, int64_t ldw, int64_t ldo, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const float* __restrict__ qa,
@@ -664,14 +673,14 @@ __global__ void __launch_bounds__(256, MINB) k_spmm_right_cost(
       }
       __syncwarp();
       const int cnt = min(32, ee - base);
-      for (int u = 0; u < cnt; u += kGU) {
-        float4 w[kGU];
+      for (int u = 0; u < cnt; u += GU) {
+        float4 w[GU];
 #pragma unroll
-        for (int k = 0; k < kGU; ++k)
+        for (int k = 0; k < GU; ++k)
           if (u + k < cnt)
             w[k] = __ldg(reinterpret_cast<const float4*>(wbase + (int64_t)my[u + k].nb * ldw * 2));
 #pragma unroll
-        for (int k = 0; k < kGU; ++k) {
+        for (int k = 0; k < GU; ++k) {
           if (u + k < cnt) {
             const EdgeRec er = lds_edge(&my[u + k]);
             if (er.seg != cur) {
@@ -766,17 +775,21 @@ fa_status launch_spmm_right_cost(const DevGraph& g2, int n1, int64_t ldw,
                                  cudaStream_t s) {
   // resident CTAs per SM the register budget is sized for: 3 (80 registers)
   // measured faster than 2 (88) on GB300 at 10k and 50k
-  static const int minb = [] {
-    const char* v = getenv("FA_PASSB_MINB");
-    return (v && atoi(v) == 2) ? 2 : 3;
-  }();
+  // Resident CTAs per SM the register budget is sized for, and gathers in
+  // flight per warp.  Measured on GB300 (one outer iteration, 50k BF16):
+  // 4 CTAs x 6 gathers (64 registers) 49.4 ms, 4 x 4 49.8 ms, 3 x 8 (80
+  // registers) 56.1 ms, 2 x 16 (128 registers) 72.3 ms: the gathers' latency
+  // is hidden by more warps, not by deeper warps.  FA_PASSB_MINB=3 selects
+  // 3 x 8 (tuning).
+  const char* mb = getenv("FA_PASSB_MINB");
+  const int minb = (mb && atoi(mb) == 3) ? 3 : 4;
   dim3 grid((unsigned)(ldo / kCT), (unsigned)((n1 + kRT - 1) / kRT));
-#define FA_PB(T, M) \
-  k_spmm_right_cost<T, M><<<grid, 256, 0, s>>>(n1, g2.n, ldw, ldo, g2.row_ptr, g2.col, qa, qb, scale, Wt, ep)
+#define FA_PB(T, M, GU) \
+  k_spmm_right_cost<T, M, GU><<<grid, 256, 0, s>>>(n1, g2.n, ldw, ldo, g2.row_ptr, g2.col, qa, qb, scale, Wt, ep)
   if (k_bf16) {
-    if (minb == 3) FA_PB(__nv_bfloat16, 3); else FA_PB(__nv_bfloat16, 2);
+    if (minb == 4) FA_PB(__nv_bfloat16, 4, 6); else FA_PB(__nv_bfloat16, 3, 8);
   } else {
-    if (minb == 3) FA_PB(float, 3); else FA_PB(float, 2);
+    if (minb == 4) FA_PB(float, 4, 6); else FA_PB(float, 3, 8);
   }
 #undef FA_PB
   FA_LAUNCHED("k_spmm_right_cost");
