@@ -777,19 +777,19 @@ fa_status launch_spmm_right_cost(const DevGraph& g2, int n1, int64_t ldw,
   // measured faster than 2 (88) on GB300 at 10k and 50k
   // Resident CTAs per SM the register budget is sized for, and gathers in
   // flight per warp.  Measured on GB300 (one outer iteration, 50k BF16):
-  // 4 CTAs x 6 gathers (64 registers) 49.4 ms, 4 x 4 49.8 ms, 3 x 8 (80
-  // registers) 56.1 ms, 2 x 16 (128 registers) 72.3 ms: the gathers' latency
-  // is hidden by more warps, not by deeper warps.  FA_PASSB_MINB=3 selects
-  // 3 x 8 (tuning).
+  // 5 CTAs x 4 gathers (48 registers; 5 x 45 KB of shared memory fit the
+  // SM) 46.1 ms, 4 x 6 48.8 ms, 3 x 8 56.1 ms, 2 x 16 72.3 ms: the gathers'
+  // latency is hidden by more warps, not by deeper warps.  FA_PASSB_MINB=4
+  // or 3 selects those shapes (tuning).
   const char* mb = getenv("FA_PASSB_MINB");
-  const int minb = (mb && atoi(mb) == 3) ? 3 : 4;
+  const int minb = (mb && atoi(mb) == 3) ? 3 : (mb && atoi(mb) == 4) ? 4 : 5;
   dim3 grid((unsigned)(ldo / kCT), (unsigned)((n1 + kRT - 1) / kRT));
 #define FA_PB(T, M, GU) \
   k_spmm_right_cost<T, M, GU><<<grid, 256, 0, s>>>(n1, g2.n, ldw, ldo, g2.row_ptr, g2.col, qa, qb, scale, Wt, ep)
   if (k_bf16) {
-    if (minb == 4) FA_PB(__nv_bfloat16, 4, 6); else FA_PB(__nv_bfloat16, 3, 8);
+    if (minb == 4) FA_PB(__nv_bfloat16, 4, 6); else if (minb == 5) FA_PB(__nv_bfloat16, 5, 4); else FA_PB(__nv_bfloat16, 3, 8);
   } else {
-    if (minb == 4) FA_PB(float, 4, 6); else FA_PB(float, 3, 8);
+    if (minb == 4) FA_PB(float, 4, 6); else if (minb == 5) FA_PB(float, 5, 4); else FA_PB(float, 3, 8);
   }
 #undef FA_PB
   FA_LAUNCHED("k_spmm_right_cost");

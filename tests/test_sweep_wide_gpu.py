@@ -130,3 +130,47 @@ def test_tensor_core_sweep_shapes_match_oracle(ragged, monkeypatch, env):
     print(f"plan {plan}: max |d log u| {du:.2e}, max |d log v| {dv:.2e}")
     assert it == ITERS and st == 0
     assert du <= 1e-4 and dv <= 1e-4
+
+
+# the planner's own shapes at other widths (its cluster rule picks a
+# power-of-two cluster with two rows per step at 30k and 70k columns, ten
+# CTAs with one row at 100k): 700 rows (a partial last step), FP64 oracle
+PLANNER_WIDTHS = (30_000, 70_000, 100_000)
+
+
+@pytest.mark.parametrize("n2", PLANNER_WIDTHS)
+def test_planner_shapes_at_other_widths_match_oracle(monkeypatch, n2):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_11952_gb300 import _lib as L
+    from paper_2607_11952_gb300 import api
+    for k in ("FA_SWEEP_Q", "FA_SWEEP_R", "FA_SWEEP_NS", "FA_SWEEP_ANYQ", "FA_SWEEP_KIND"):
+        monkeypatch.delenv(k, raising=False)
+    n1 = 700
+    rng = synth.rng_for(3000 + n2 // 1000)
+    K = synth.random_kernel_rows(n1, n2, rng)
+    lv0 = synth.random_log_scalings(n2, rng)
+    mu, nu = np.full(n1, 1.0 / n1), np.full(n2, 1.0 / n2)
+    u, v, _ = R.sinkhorn_scaling(K.astype(np.float64), mu, nu, ITERS,
+                                 v0=np.exp(lv0.astype(np.float64)), track_err=False)
+    empty = np.zeros((0, 2), np.int64)
+    al = api.Aligner(api.Graph(n1, empty), api.Graph(n2, empty), api.Params(dtype="bf16"))
+    try:
+        plan = L.fa_sweep_plan(n1, al.ld, L.FA_BF16)
+        al.K.zero_()
+        al.K[:, :n2].copy_(torch.from_numpy(K).to(al.device).to(al.K.dtype))
+        al.log_v.copy_(torch.from_numpy(lv0))
+        it, err, st = al.sinkhorn(ITERS)
+        torch.cuda.synchronize()
+        lu, lv = al.log_u.double().cpu().numpy(), al.log_v.double().cpu().numpy()
+    finally:
+        al.close()
+    expect = {30_000: (4, 2), 70_000: (8, 2), 100_000: (10, 1)}[n2]
+    assert (plan["Q"], plan["R"]) == expect, plan
+    assert it == ITERS and st == 0
+    du = np.abs(lu - np.log(u)).max()
+    dv = np.abs(lv - np.log(v)).max()
+    print(f"n2 {n2} plan {plan}: max |d log u| {du:.2e}, max |d log v| {dv:.2e}")
+    assert du <= 1e-4 and dv <= 1e-4
