@@ -29,3 +29,24 @@ def test_reference_arm_json_line():
     import bench
     a = argparse.Namespace(config="cl50k", outer=30, tol=1e-4, check_every=5)
     assert d["config"] == bench._config(a, 1)
+
+
+def test_sweep_traffic_is_reported_only_for_the_captured_kernel_and_width(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu record only while the
+    sweep's source hashes to the recorded value and the row width is the
+    captured one; it scales with the rows."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "k_sweep_traffic.json")))
+    a = argparse.Namespace(dtype="bf16")
+    got = bench._ncu_traffic(a, 50_000, 50_000)
+    if rec["source_sha256"] == bench.sweep_source_hash():
+        assert got == rec["bf16"]["dram_bytes_per_launch_captured"] * 10
+        assert abs(got - 5.0e9) / 5.0e9 < 0.02          # the algorithmic bytes
+        assert bench._ncu_traffic(a, 25_000, 50_000) == got // 2
+    else:
+        assert got is None
+    assert bench._ncu_traffic(a, 100_000, 80_000) is None   # another launch shape
+    monkeypatch.setattr(bench, "sweep_source_hash", lambda: "0" * 64)
+    assert bench._ncu_traffic(a, 50_000, 50_000) is None    # another kernel source
