@@ -11,8 +11,9 @@
 //   at the end:        v_j = nu_j / colacc_j                      (a update)
 //
 // The row sum must be complete before its column contributions are added,
-// so a row is owned by one thread-block cluster of Q CTAs; CTA q owns the
-// column slab [q W, (q+1) W) and keeps the matching slice of v and of the
+// so a row is owned by one thread-block cluster of Q CTAs; CTA q owns a
+// column slab (the row's 16-byte units split over the Q CTAs as evenly as
+// possible, W the widest slab) and keeps the matching slice of v and of the
 // column accumulators in registers for the whole sweep.  Rows arrive through
 // a ring of NS shared-memory stages filled by TMA bulk copies (one producer
 // thread, mbarrier completion), so HBM latency is hidden by the ring depth,
