@@ -466,8 +466,8 @@ fa_status launch_spmm_left_T(const DevGraph& g1, int n2, int64_t ldd,
                              float* Wt, cudaStream_t s) {
   const bool two = vb != nullptr;
   // measured at 50k on GB300: the row-per-warp form is faster for the two
-  // value sets of Pass A in BF16 (17 vs 22 ms) and takes them always; for
-  // one value set (propagation) the forms are equal and FA_PASSA_ROWS=1
+  // value sets of Pass A in BF16 (14 vs 22 ms) and takes them always; for
+  // one value set (propagation) the forms were equal and FA_PASSA_ROWS=1
   // selects the row form
   static const int form = [] {
     const char* v = getenv("FA_PASSA_ROWS");
